@@ -1,0 +1,313 @@
+"""Benchmark of the fused LB step for the Kuramoto-Sivashinsky equation on GB300.
+
+Workload (default): the D1Q7 ensemble of 4096 independent periodic lattices,
+N log-uniform in [256, 8192] (9.4 M sites in all), dx = 0.1, dt = 1e-4,
+tau ~ U(1.5, 3), 16 random modes of amplitude <= 1e-2, populations stored in
+FP32 with FP64 mass guard every 500 steps, run by the register-resident
+persistent kernel.  One benchmark step = 1000 LB time steps of every lattice.
+Metric: lattice-site updates per second (whole job).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (torchrun) each rank runs
+its own ensemble (weak scaling; the runs are independent, no collective on
+the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LB_STEPS_PER_STEP = 1000
+GUARD_EVERY = 500
+FLOP_PER_SITE_UPDATE = {7: 39, 5: 27}  # folded step, FMA = 2 flops: 6Q - 3
+SM_COUNT_NOMINAL = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--nruns", type=int, default=4096)
+    p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(wl, sample_runs=64, sample_steps=3000):
+    """The FP64 oracle, as it stands, on the host cores, on a bounded sample."""
+    from oracle import lbks as ora
+
+    idx = np.linspace(0, wl.nruns - 1, sample_runs).astype(int)
+    sub = wl.subset(idx)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    _, used = ora.run_batch(sub.scheme, sub.N, sub.L / sub.N, sub.dt, sub.tau, sub.rho0, sample_steps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sub.sites * sample_steps / dt, "unit": "site-updates/s", "cores": used, "kind": "oracle",
+            "sample": f"{sample_runs} of {wl.nruns} runs ({sub.sites} sites), {sample_steps} steps, FP64",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1711_03540_gb300 import workloads
+
+    wl = workloads.ensemble(nruns=args.nruns)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(wl, sample_runs=8, sample_steps=50)
+    t_all = 0.0
+    for _ in range(args.steps):
+        r = cpu_baseline(wl, sample_runs=16, sample_steps=100)
+        vals.append(r["value"])
+        t_all += r["seconds"]
+    v = float(statistics.median(vals))
+    line = {"impl": "reference", "metric": "lattice-site updates/s", "value": v, "unit": "site-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sample": "16 runs x 100 LB steps per step"},
+            "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "16 of 4096 runs (evenly spaced), 100 LB steps, FP64"},
+            "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_1711_03540_gb300 as lb
+    from paper_1711_03540_gb300 import build as lbbuild
+    from paper_1711_03540_gb300 import workloads
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lbbuild.build()
+    stream = torch.cuda.Stream()
+    wl = workloads.ensemble(nruns=args.nruns, seed=workloads.BASE_SEED + rank * args.nruns)
+    Q = wl.scheme
+    opts = lb.lb_ks_default_opts(precision=lb.F32, recentre_every=GUARD_EVERY, kernel=lb.KERNEL_RESIDENT,
+                                 stream=stream)
+    h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
+    desc = lb.lb_ks_describe(h)
+    sites = wl.sites
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lb.lb_ks_step(h, LB_STEPS_PER_STEP)
+        barrier()
+        launches0 = lb.lb_ks_launches(h)
+        clk = ClockSampler(local)
+        clk.start()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for i in range(args.steps):
+            lb.lb_ks_step(h, LB_STEPS_PER_STEP)
+            ev[i + 1].record(stream)
+        barrier()
+        clocks = clk.stop()
+        launches = lb.lb_ks_launches(h) - launches0
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = sites * LB_STEPS_PER_STEP * args.steps
+    value = updates * ws / (total_ms * 1e-3)
+
+    # Roofline of the dominant kernel (the resident kernel): FP32 ALU.
+    k = desc["steps_per_launch"]
+    res_launches_per_step = -(-LB_STEPS_PER_STEP // k)
+    launch_ms = statistics.mean(step_ms) / res_launches_per_step  # guard kernels (<1%) are charged to it
+    flops_per_launch = FLOP_PER_SITE_UPDATE[Q] * sites * k
+    smax = clocks.get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(local)
+    peak_tflops = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12
+    achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "traffic": None, "kernel": "resident_kernel<7,F32,%d>" % desc["sites_per_thread"],
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (derived)",
+                "algorithmic": f"{FLOP_PER_SITE_UPDATE[Q]} flop/site-update x {sites} sites x {k} steps per launch"}
+    line = {"metric": "lattice-site updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "scheme": "D1Q7", "nruns": wl.nruns, "sites": sites,
+                       "lb_steps_per_step": LB_STEPS_PER_STEP, "storage": "f32 deviations", "guard_every": GUARD_EVERY,
+                       "kernel": "resident", "sites_per_thread": desc["sites_per_thread"],
+                       "threads_per_block": desc["threads_per_block"], "steps_per_launch": k,
+                       "l2": f"state {sites * Q * 4 / 1e6:.0f} MB > 129 MB L2 (no flush needed)"},
+            "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches)}
+
+    if not args.no_extras and rank == 0:
+        extras(lb, torch, wl, h, stream, line, local)
+    lb.lb_ks_free(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def extras(lb, torch, wl, h_res, stream, line, local):
+    Q = wl.scheme
+    sites = wl.sites
+    # Plain FP64 kernel on the same ensemble (the FP64 baseline), and the error of the
+    # FP32 resident run against it after the same number of steps.
+    nref = 1000
+    o64 = lb.lb_ks_default_opts(precision=lb.F64, kernel=lb.KERNEL_PLAIN, stream=stream)
+    h64 = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, o64)
+    o32 = lb.lb_ks_default_opts(precision=lb.F32, recentre_every=GUARD_EVERY, kernel=lb.KERNEL_RESIDENT, stream=stream)
+    h32 = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, o32)
+    with torch.cuda.stream(stream):
+        lb.lb_ks_step(h64, 100)  # warm-up + graph capture
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lb.lb_ks_step(h64, nref - 100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        lb.lb_ks_step(h32, nref)
+        r64, r32 = np.empty(sites), np.empty(sites)
+        lb.lb_ks_rho(h64, r64)
+        lb.lb_ks_rho(h32, r32)
+    lb.lb_ks_free(h64)
+    lb.lb_ks_free(h32)
+    v64 = sites * (nref - 100) / (ms64 * 1e-3)
+    off = wl.offsets()
+    per = [np.linalg.norm(r32[off[i]:off[i + 1]] - r64[off[i]:off[i + 1]]) /
+           max(np.linalg.norm(r64[off[i]:off[i + 1]]), 1e-300) for i in range(wl.nruns)]
+    line["plain_fp64"] = {"value": v64, "unit": "site-updates/s", "kernel": "plain_step_kernel<7,F64>",
+                          "steps_timed": nref - 100}
+    line["vs_plain_fp64"] = line["value"] / v64 if line["n_gpus"] == 1 else None
+    line["error"] = {"vs": "FP64 plain kernel (parity-tested against the oracle)", "lb_steps": nref,
+                     "rel_l2_global": float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64)),
+                     "rel_l2_max_run": float(max(per)), "tolerance": 1e-4}
+
+    # End to end through the C ABI with host buffers: per step, batch_init from
+    # pinned host rho0 (H2D), LB_STEPS_PER_STEP steps, rho to pinned host (D2H).
+    rho_host = torch.from_numpy(wl.rho0).pin_memory()
+    out_host = torch.empty(sites, dtype=torch.float64).pin_memory()
+    o = lb.lb_ks_default_opts(precision=lb.F32, recentre_every=GUARD_EVERY, kernel=lb.KERNEL_RESIDENT, stream=stream)
+    reps = 3
+    times = []
+    for rep in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        he = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, rho_host, o)
+        lb.lb_ks_step(he, LB_STEPS_PER_STEP)
+        lb.lb_ks_rho(he, out_host)
+        lb.lb_ks_free(he)
+        if rep:
+            times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(times)
+    line["e2e"] = {"value": sites * LB_STEPS_PER_STEP / e2e_s, "unit": "site-updates/s",
+                   "h2d_bytes_per_step": int(rho_host.numel() * 8 + wl.nruns * 32),
+                   "d2h_bytes_per_step": int(out_host.numel() * 8),
+                   "includes": "lb_ks_batch_init (host rho0 -> device, allocation, planning), "
+                               f"{LB_STEPS_PER_STEP} steps, lb_ks_rho to host, lb_ks_free"}
+    line["cpu_baseline"] = cpu_baseline(wl)
+    try:
+        line["fma_peak_measured_tflops"] = {"fp32": lb.lb_ks_fma_peak(False) / 1e12, "fp64": lb.lb_ks_fma_peak(True) / 1e12}
+    except Exception as exc:  # diagnostic only
+        line["fma_peak_measured_tflops"] = str(exc)
+
+
+if __name__ == "__main__":
+    main()

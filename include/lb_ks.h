@@ -1,0 +1,215 @@
+/*
+ * lb_ks.h -- C ABI of the GB300 (sm_103a) library for the lattice Boltzmann
+ * scheme for the Kuramoto-Sivashinsky equation of Otomo, Boghosian & Dubois,
+ * "Efficient lattice Boltzmann models for the Kuramoto-Sivashinsky equation"
+ * (arXiv:1711.03540).
+ *
+ * The library advances periodic lattices with the BGK lattice Boltzmann
+ * equation (Sec. 2, Eq. LB_equation_ordinary)
+ *     f_i(x + c_i, t + 1) - f_i(x, t) = -(f_i - f^eq_i) / tau,
+ *     f^eq_i = rho (w0_i + K w2_i + M' w4_i + E w6_i) + rho^2 J w1_i,  rho = sum_i f_i,
+ * on D1Q5 (c = 0, +-1, +-2; M' = M, E = 0; Eq. feq) or D1Q7
+ * (c = 0, +-1, +-2, +-3; M' = M + delta M, E = 120 beta (T1+1)/((T4+1) alpha^4);
+ * Sec. 2.3), with J, K, M from Table 2, T_i from Eq. T_form and the scaling
+ * X = alpha x, T = beta t (Eq. scaling): alpha = L / N, beta = dt.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns a status code (LB_KS_OK or a negative LB_KS_E*);
+ *    no C++ exception crosses this boundary.  lb_ks_last_error() gives a
+ *    one-line reason for the last failure on a handle.
+ *  - A handle owns its device memory (allocated in lb_ks_init /
+ *    lb_ks_batch_init, released by lb_ks_free).  It never keeps or frees a
+ *    pointer the caller passes in.  Input and output pointers may be host or
+ *    device memory of the current device; the library tells them apart with
+ *    cudaPointerGetAttributes.
+ *  - Work is issued on the stream given in lb_ks_opts (NULL = the legacy
+ *    default stream).  lb_ks_step returns without waiting; lb_ks_rho,
+ *    lb_ks_mass_energy and lb_ks_save wait for the stream.
+ *  - Errors detected on the device (a non-finite FP64 mass at a guard step)
+ *    are sticky: they are reported by the next call that waits, and every
+ *    later call on the handle returns the same code.
+ *  - One handle must not be used from two host threads at once.
+ *  - There is no CPU fallback.  Without a usable CUDA device the
+ *    constructors return LB_KS_ECUDA.
+ */
+#ifndef LB_KS_H
+#define LB_KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+/* Symbols of the C ABI stay visible when the library is built with hidden default visibility. */
+#if defined(__GNUC__)
+#define LB_KS_API __attribute__((visibility("default")))
+#else
+#define LB_KS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define LB_KS_OK 0
+#define LB_KS_EINVAL (-1)    /* invalid argument; nothing was done */
+#define LB_KS_ENOMEM (-2)    /* device or host allocation failed */
+#define LB_KS_ECUDA (-3)     /* CUDA runtime error, or no usable device */
+#define LB_KS_EUNSTABLE (-4) /* non-finite FP64 mass found at a guard step (sticky) */
+#define LB_KS_ETIMEOUT (-5)  /* reserved: a bounded device wait ran out (sticky) */
+
+/* Lattice schemes (Sec. 2.3): the number of speeds. */
+#define LB_KS_D1Q5 5
+#define LB_KS_D1Q7 7
+
+/* Storage precision of the populations.
+ * F64: FP64 storage and arithmetic.
+ * F32: FP32 storage of f_i - w0_i rho_bar (rho_bar = the run's initial mean;
+ *      w0 = (1, 0, ...), so only f_0 is offset), FP32 arithmetic.
+ * F16S: the same deviations stored as FP16 times a per-run scale, FP32 arithmetic.
+ * In F32 and F16S the FP64 mass guard (recentre_every) restores the run's
+ * initial mass. */
+#define LB_KS_F64 0
+#define LB_KS_F32 1
+#define LB_KS_F16S 2
+
+/* Kernel family. */
+#define LB_KS_KERNEL_AUTO 0     /* resident when every run fits its constraints, else plain (F64) / stream */
+#define LB_KS_KERNEL_PLAIN 1    /* one thread per site, one launch per step (F64, F32) */
+#define LB_KS_KERNEL_STREAM 2   /* HBM-streaming tiles, one launch per step (F32, F16S) */
+#define LB_KS_KERNEL_RESIDENT 3 /* register-resident, many steps per launch (F64, F32, F16S) */
+
+/* Reading of Eq. delta_M. */
+#define LB_KS_DM_DERIVED 0 /* bracket (T2+1)/(2(T1+1)) - (T3+1)/(T2+1), as Eq. KS_trunc2 needs */
+#define LB_KS_DM_PRINTED 1 /* bracket with (T3+1)/(T4+1) as printed */
+
+typedef struct lb_ks lb_ks_t; /* opaque handle */
+
+typedef struct lb_ks_opts {
+    int32_t precision;         /* LB_KS_F64 (default), LB_KS_F32, LB_KS_F16S */
+    int32_t dm_variant;        /* LB_KS_DM_DERIVED (default) or LB_KS_DM_PRINTED */
+    int32_t recentre_every;    /* R > 0: every R steps compute the FP64 mass of every run and add
+                                  (M0 - M)/N to f_0 at each site; 0 = never (default for F64) */
+    int32_t kernel;            /* LB_KS_KERNEL_* */
+    int32_t steps_per_launch;  /* resident kernel: steps kept on chip per launch; 0 = auto */
+    int32_t sites_per_thread;  /* resident kernel: register slots per thread (4,6,8,12,16 for
+                                  F32/F16S; 4,6,8 for F64); 0 = auto */
+    int32_t threads_per_block; /* resident kernel: 128, 256 or 512; 0 = auto */
+    int32_t use_graph;         /* 1 (default): replay captured CUDA graphs for step sequences */
+    void *stream;              /* cudaStream_t; NULL = legacy default stream */
+} lb_ks_opts;
+
+/* Fill *opts with the defaults listed above. */
+LB_KS_API void lb_ks_default_opts(lb_ks_opts *opts);
+
+/*
+ * Host precompute of one run's constants (no GPU needed).
+ * Sec. 2: T1..T4 (Eq. T_form), J, K, M (Table 2), delta M (Eq. delta_M),
+ * E (delta f^eq, Sec. 2.2), with alpha = dx and beta = dt (Eq. scaling).
+ *   A[i], B[i] (i < scheme): f^eq_i(rho) = A_i rho + B_i rho^2.
+ *   coef[9] (may be NULL): T1, T2, T3, T4, J, K, M, delta M, E.
+ * Returns LB_KS_EINVAL for an unknown scheme, dx <= 0, dt <= 0, tau <= 1/2
+ * or a non-finite result (T4 + 1 = 0 near tau = 0.908).
+ */
+LB_KS_API int lb_ks_params(int scheme, double dx, double dt, double tau, int dm_variant, double *A, double *B,
+                 double *coef);
+
+/*
+ * Minimum stable relaxation time fitted in Sec. 3 (Eq. general_tau_formula with
+ * Eq. A_B_fit_D1Q5 / Eq. A_B_fit_D1Q7) for lattice spacing dX and time step dT.
+ * Returns NaN for an unknown scheme or non-positive dX, dT.  The fit was made
+ * on the paper's front test; it is advice, not a stability guarantee.
+ */
+LB_KS_API double lb_ks_tau_fit(int scheme, double dX, double dT);
+
+/*
+ * Create a handle for one periodic lattice of N sites on [0, L):
+ * alpha = L / N, beta = dt, relaxation time tau (>= 1; T4 + 1 vanishes near
+ * 0.908 and the paper uses tau >= 1, Sec. 3), and initial density
+ * rho0[N] (FP64, host or device, read once).  Populations start at
+ * equilibrium, f_i = f^eq_i(rho0).  opts may be NULL (defaults).
+ * Errors: LB_KS_EINVAL (unknown scheme, N < 2 c_max + 1, L <= 0, dt <= 0,
+ * tau < 1, non-finite rho0, bad opts), LB_KS_ENOMEM, LB_KS_ECUDA.  On error
+ * *h is set to NULL.
+ */
+LB_KS_API int lb_ks_init(lb_ks_t **h, int scheme, int64_t N, double L, double dt, double tau, const double *rho0,
+               const lb_ks_opts *opts);
+
+/*
+ * Create a handle for nruns independent periodic lattices advanced together
+ * (one ensemble).  Run r has N[r] sites on [0, L[r]), time step dt[r] and
+ * relaxation time tau[r]; rho0 holds the initial densities of all runs
+ * concatenated in run order (sum N[r] values, FP64, host or device).
+ * The same argument rules and errors as lb_ks_init apply to every run.
+ */
+LB_KS_API int lb_ks_batch_init(lb_ks_t **h, int scheme, int32_t nruns, const int64_t *N, const double *L,
+                     const double *dt, const double *tau, const double *rho0, const lb_ks_opts *opts);
+
+/*
+ * Advance every run of the handle by n >= 0 time steps of
+ * Eq. LB_equation_ordinary (each step: rho = sum_i f_i, f^eq, BGK collision,
+ * periodic shift of f_i by c_i).  Asynchronous on the handle's stream.
+ * Errors: LB_KS_EINVAL (n < 0), LB_KS_ECUDA, or a sticky error.
+ */
+LB_KS_API int lb_ks_step(lb_ks_t *h, int64_t n);
+
+/*
+ * Write rho = sum_i f_i at every site (FP64; runs concatenated in run order,
+ * sum N[r] values) to out (host or device, caller-owned).  Waits for the stream.
+ */
+LB_KS_API int lb_ks_rho(lb_ks_t *h, double *out);
+
+/*
+ * FP64 mass sum_x rho(x) and energy sum_x rho(x)^2 of every run
+ * (arrays of nruns values, host memory).  Either pointer may be NULL.
+ * Waits for the stream; returns LB_KS_EUNSTABLE if a mass is not finite.
+ */
+LB_KS_API int lb_ks_mass_energy(lb_ks_t *h, double *mass, double *energy);
+
+/* Number of bytes lb_ks_save writes for this handle. */
+LB_KS_API int lb_ks_state_bytes(const lb_ks_t *h, size_t *bytes);
+
+/*
+ * Checkpoint: copy the full state (populations in their storage precision,
+ * the step counter and the guard's reference masses) to buf (host memory of
+ * at least lb_ks_state_bytes bytes).  lb_ks_load restores it into a handle
+ * created with the same runs, scheme and precision.  Resuming from a
+ * checkpoint gives bitwise the same result as running straight through.
+ */
+LB_KS_API int lb_ks_save(lb_ks_t *h, void *buf, size_t bytes);
+LB_KS_API int lb_ks_load(lb_ks_t *h, const void *buf, size_t bytes);
+
+/* Steps advanced since init (or since the loaded checkpoint's start). */
+LB_KS_API int64_t lb_ks_steps_done(const lb_ks_t *h);
+
+/*
+ * Describe the handle: kernel family actually used (LB_KS_KERNEL_*), resident
+ * sites per thread, threads per block and steps per launch (0 when not
+ * resident), number of runs and total sites.  Any pointer may be NULL.
+ */
+LB_KS_API int lb_ks_describe(const lb_ks_t *h, int *kernel, int *sites_per_thread, int *threads_per_block,
+                   int *steps_per_launch, int32_t *nruns, int64_t *total_sites);
+
+/* Kernel launches issued by this handle since creation (a counter kept on the host). */
+LB_KS_API int64_t lb_ks_launches(const lb_ks_t *h);
+
+/*
+ * Diagnostic (no counterpart in the paper): measured throughput of the FP32
+ * (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add pipes of the current device
+ * in flop/s, from a short kernel of independent FMA chains.  Used to put the
+ * resident kernel's arithmetic rate next to the machine's.  Allocates and
+ * frees a small device buffer.  Errors: LB_KS_EINVAL, LB_KS_ECUDA.
+ */
+LB_KS_API int lb_ks_fma_peak(int fp64, double *flops_per_s);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+LB_KS_API void lb_ks_free(lb_ks_t *h);
+
+/* One-line reason for the last failure on h (or on the last failed
+ * constructor when h is NULL).  Never NULL; valid until the next call on h. */
+LB_KS_API const char *lb_ks_last_error(const lb_ks_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_KS_H */

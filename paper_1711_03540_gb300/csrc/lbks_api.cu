@@ -1,0 +1,717 @@
+// Host side of the C ABI (include/lb_ks.h): handle, validation, memory
+// layout, work planning, step scheduling with CUDA-graph replay, guard,
+// checkpointing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lb_ks.h"
+#include "lbks_internal.h"
+
+namespace lbks {
+int stream_tile_sites();
+cudaError_t stream_prepare(int Q, int storage);
+}
+
+using namespace lbks;
+
+namespace {
+
+thread_local std::string g_ctor_error = "no error";
+
+constexpr int kPlainTile = 256;
+constexpr int kAlign = 32;  // elements: run offsets and the plane stride are multiples of this
+constexpr uint32_t kMagic = 0x534b424cu;  // "LBKS"
+constexpr uint32_t kVersion = 1;
+
+struct GraphEntry {
+  int64_t n, phase;
+  int cur_in, cur_out;
+  int64_t kernels;
+  cudaGraphExec_t exec;
+};
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+size_t storage_bytes(int prec) { return prec == kF64 ? 8 : (prec == kF32 ? 4 : 2); }
+
+}  // namespace
+
+struct lb_ks {
+  int Q = 0, prec = 0, kernel = 0, cmax = 0;
+  lb_ks_opts opts{};
+  int32_t nruns = 0;
+  std::vector<int64_t> N, rho_off;
+  std::vector<RunDesc> runs_h;
+  std::vector<double> mass0_h;
+  int64_t total_sites = 0, plane = 0;
+  void* fbuf[2] = {nullptr, nullptr};
+  int cur = 0;
+  RunDesc* d_runs = nullptr;
+  Tile* d_plain_tiles = nullptr;
+  int n_plain_tiles = 0;
+  Tile* d_stream_tiles = nullptr;
+  int n_stream_tiles = 0;
+  int32_t* d_stream_tile_begin = nullptr;
+  int64_t* d_rho_off = nullptr;
+  double* d_stage = nullptr;
+  double* d_partials = nullptr;
+  double* d_mass0 = nullptr;
+  double* d_mass = nullptr;
+  double* d_energy = nullptr;
+  double* d_delta = nullptr;
+  int* d_flags = nullptr;
+  // resident kernel
+  int S = 0, NT = 0, kmax = 0, grid = 0, nbundles = 0;
+  Piece* d_pieces = nullptr;
+  int2* d_bundles = nullptr;
+  int* d_queue = nullptr;
+  // scheduling
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int64_t steps_done = 0;
+  int64_t phase = 0;  // steps since the last guard
+  int64_t launches = 0;
+  int sticky = LB_KS_OK;
+  std::string err = "no error";
+  std::vector<GraphEntry> graphs;
+  std::vector<void*> allocations;
+};
+
+namespace {
+
+int fail(lb_ks* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_ctor_error = msg;
+  return code;
+}
+
+int cuda_fail(lb_ks* h, cudaError_t e, const char* what) {
+  return fail(h, LB_KS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBKS_CUDA(h, call, what)                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+template <typename T>
+int dalloc(lb_ks* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, LB_KS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  h->allocations.push_back(*p);
+  return LB_KS_OK;
+}
+
+Arena arena(lb_ks* h, int which) { return Arena{h->fbuf[which], h->plane}; }
+
+bool valid_opts(const lb_ks_opts& o, std::string* why) {
+  if (o.precision < LB_KS_F64 || o.precision > LB_KS_F16S) { *why = "opts.precision must be 0, 1 or 2"; return false; }
+  if (o.dm_variant != LB_KS_DM_DERIVED && o.dm_variant != LB_KS_DM_PRINTED) { *why = "opts.dm_variant must be 0 or 1"; return false; }
+  if (o.recentre_every < 0) { *why = "opts.recentre_every must be >= 0"; return false; }
+  if (o.kernel < LB_KS_KERNEL_AUTO || o.kernel > LB_KS_KERNEL_RESIDENT) { *why = "opts.kernel must be 0..3"; return false; }
+  if (o.steps_per_launch < 0) { *why = "opts.steps_per_launch must be >= 0"; return false; }
+  if (o.sites_per_thread != 0 && o.sites_per_thread != 4 && o.sites_per_thread != 6 && o.sites_per_thread != 8 &&
+      o.sites_per_thread != 12 && o.sites_per_thread != 16) {
+    *why = "opts.sites_per_thread must be 0, 4, 6, 8, 12 or 16"; return false;
+  }
+  if (o.threads_per_block != 0 && (o.threads_per_block < 32 || o.threads_per_block > 512 || o.threads_per_block % 32)) {
+    *why = "opts.threads_per_block must be 0 or a multiple of 32 in [32, 512]"; return false;
+  }
+  if (o.kernel == LB_KS_KERNEL_PLAIN && o.precision == LB_KS_F16S) { *why = "the plain kernel stores F64 or F32"; return false; }
+  return true;
+}
+
+// ---------------------------------------------------------------- planning
+
+// Ring or segment pieces of every run for (S, NT, k); false if some run cannot be held.
+bool plan_pieces(const lb_ks* h, int S, int NT, int k, std::vector<Piece>* out) {
+  out->clear();
+  const int C = h->cmax;
+  for (int32_t r = 0; r < h->nruns; ++r) {
+    const int64_t N = h->N[r];
+    // Ring: hold m copies of the lattice around one ring of m N sites (m > 1 only
+    // for lattices shorter than S (S-1), which cannot be cut into runs of S and
+    // S-1 sites).  Translation invariance keeps the copies bitwise identical;
+    // the first one is stored.
+    bool ring = false;
+    for (int64_t m = 1;; ++m) {
+      const int64_t n = m * N;
+      const int64_t V = (n + S - 1) / S;
+      if (V > NT) break;
+      if (n > V * (S - 1)) {
+        Piece p{};
+        p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n; p.x0 = 0; p.st_lo = 0; p.st_hi = (int)N;
+        out->push_back(p);
+        ring = true;
+        break;
+      }
+    }
+    if (ring) continue;
+    const int64_t h2 = 2LL * C * k;
+    const int64_t room = (int64_t)NT * S - h2 - 2 * S;
+    if (room <= 0) return false;
+    const int64_t nseg = (N + room - 1) / room;
+    const int64_t Ls = (N + nseg - 1) / nseg;
+    for (int64_t s0 = 0; s0 < N; s0 += Ls) {
+      const int64_t len = std::min<int64_t>(Ls, N - s0);
+      int64_t n = len + h2;
+      int64_t V = (n + S - 1) / S;
+      while (n <= V * (S - 1)) { ++n; V = (n + S - 1) / S; }
+      if (V > NT) return false;
+      Piece p{};
+      p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n;
+      p.x0 = ((s0 - (int64_t)C * k) % N + N) % N;
+      p.st_lo = C * k; p.st_hi = (int)(C * k + len);
+      out->push_back(p);
+    }
+  }
+  return true;
+}
+
+// First-fit decreasing packing of pieces into blocks of NT threads; bundles in
+// decreasing order of occupied threads (longest first).
+void pack_bundles(std::vector<Piece>& pieces, int NT, std::vector<Piece>* ordered, std::vector<int2>* bundles) {
+  std::vector<int> idx(pieces.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return pieces[a].nthr > pieces[b].nthr; });
+  std::vector<std::vector<int>> bins;
+  std::vector<int> used;
+  for (int i : idx) {
+    size_t b = 0;
+    for (; b < bins.size(); ++b)
+      if (used[b] + pieces[i].nthr <= NT) break;
+    if (b == bins.size()) { bins.emplace_back(); used.push_back(0); }
+    pieces[i].t0 = used[b];
+    used[b] += pieces[i].nthr;
+    bins[b].push_back(i);
+  }
+  std::vector<int> order(bins.size());
+  for (size_t b = 0; b < bins.size(); ++b) order[b] = (int)b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return used[a] > used[b]; });
+  ordered->clear();
+  bundles->clear();
+  for (int b : order) {
+    bundles->push_back(make_int2((int)ordered->size(), (int)bins[b].size()));
+    for (int i : bins[b]) ordered->push_back(pieces[i]);
+  }
+}
+
+int default_threads(int prec, int S) {
+  if (prec == kF64) return 256;
+  return S <= 8 ? 512 : (S <= 12 ? 384 : 256);
+}
+
+int setup_resident(lb_ks* h, bool required) {
+  std::vector<int> cand;
+  if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
+  else if (h->prec == kF64) cand = {8, 6, 4};
+  else cand = {12, 8, 16, 6, 4};
+  const int R = h->opts.recentre_every;
+  for (int S : cand) {
+    const int NT = h->opts.threads_per_block ? h->opts.threads_per_block : default_threads(h->prec, S);
+    if (!resident_supported(h->Q, h->prec, S, NT)) continue;
+    int k = h->opts.steps_per_launch;
+    std::vector<Piece> pieces;
+    if (k == 0) {
+      k = R > 0 ? std::min(R, 1000) : 1000;
+      // with segments, keep the halo work near 10% of a block's sites
+      if (!plan_pieces(h, S, NT, k, &pieces) || pieces.size() != (size_t)h->nruns) {
+        const int kseg = std::max(1, (int)((int64_t)NT * S / (20 * h->cmax)));
+        k = std::min(k, kseg);
+        if (R > 0) while (R % k) --k;  // launches end on guard steps
+      }
+    }
+    if (!plan_pieces(h, S, NT, k, &pieces)) continue;
+    std::vector<Piece> ordered;
+    std::vector<int2> bundles;
+    pack_bundles(pieces, NT, &ordered, &bundles);
+    int bps = 0;
+    cudaError_t e = resident_prepare(h->Q, h->prec, S, NT, &bps);
+    if (e != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+    int dev = 0, sms = 0;
+    LBKS_CUDA(h, cudaGetDevice(&dev), "cudaGetDevice");
+    LBKS_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    int rc;
+    if ((rc = dalloc(h, &h->d_pieces, ordered.size()))) return rc;
+    if ((rc = dalloc(h, &h->d_bundles, bundles.size()))) return rc;
+    if ((rc = dalloc(h, &h->d_queue, 1))) return rc;
+    LBKS_CUDA(h, cudaMemcpy(h->d_pieces, ordered.data(), ordered.size() * sizeof(Piece), cudaMemcpyHostToDevice), "upload pieces");
+    LBKS_CUDA(h, cudaMemcpy(h->d_bundles, bundles.data(), bundles.size() * sizeof(int2), cudaMemcpyHostToDevice), "upload bundles");
+    h->S = S;
+    h->NT = NT;
+    h->kmax = k;
+    h->nbundles = (int)bundles.size();
+    h->grid = std::min(h->nbundles, bps * sms);
+    return LB_KS_OK;
+  }
+  if (required) return fail(h, LB_KS_EINVAL, "resident kernel cannot hold these lattices with the requested tiling");
+  return 1;  // not possible; caller picks another family
+}
+
+// ---------------------------------------------------------------- step scheduling
+
+int issue_guard(lb_ks* h, cudaStream_t s, bool recentre, int64_t* nk) {
+  LBKS_CUDA(h, launch_mass_partials(h->Q, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles,
+                                    h->n_stream_tiles, h->d_partials, s), "mass partials");
+  LBKS_CUDA(h, launch_mass_finalize(h->nruns, h->d_stream_tile_begin, h->d_partials, h->d_runs, h->d_mass0, h->d_mass,
+                                    h->d_energy, recentre ? h->d_delta : nullptr, h->d_flags, s), "mass finalize");
+  *nk += 2;
+  if (recentre) {
+    LBKS_CUDA(h, launch_recentre(h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles, h->n_stream_tiles,
+                                 h->d_delta, s), "recentre");
+    *nk += 1;
+  }
+  return LB_KS_OK;
+}
+
+// Issue n steps on stream s, updating cur / phase / steps_done as the work will.
+int issue_steps(lb_ks* h, int64_t n, cudaStream_t s, int64_t* nk) {
+  const int64_t R = h->opts.recentre_every;
+  while (n > 0) {
+    int64_t k = 1;
+    if (h->kernel == LB_KS_KERNEL_RESIDENT) {
+      k = std::min<int64_t>(n, h->kmax);
+      if (R > 0) k = std::min<int64_t>(k, R - h->phase);
+      LBKS_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), s), "queue reset");
+      ResidentLaunch L{h->Q, h->prec, h->S, h->NT, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
+                       h->d_pieces, h->d_bundles, h->nbundles, h->d_queue, (int)k, h->grid};
+      LBKS_CUDA(h, launch_resident(L, s), "resident step");
+    } else if (h->kernel == LB_KS_KERNEL_STREAM) {
+      LBKS_CUDA(h, launch_stream_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
+                                      h->d_stream_tiles, h->n_stream_tiles, s), "stream step");
+    } else {
+      LBKS_CUDA(h, launch_plain_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
+                                     h->d_plain_tiles, h->n_plain_tiles, s), "plain step");
+    }
+    *nk += 1;
+    h->cur = 1 - h->cur;
+    n -= k;
+    h->steps_done += k;
+    if (R > 0) {
+      h->phase += k;
+      if (h->phase == R) {
+        h->phase = 0;
+        int rc = issue_guard(h, s, true, nk);
+        if (rc) return rc;
+      }
+    }
+  }
+  return LB_KS_OK;
+}
+
+int run_chunk_graph(lb_ks* h, int64_t n) {
+  for (auto& g : h->graphs) {
+    if (g.n == n && g.phase == h->phase && g.cur_in == h->cur) {
+      LBKS_CUDA(h, cudaGraphLaunch(g.exec, h->stream), "graph launch");
+      h->cur = g.cur_out;
+      h->steps_done += n;
+      const int64_t R = h->opts.recentre_every;
+      if (R > 0) h->phase = (h->phase + n) % R;
+      h->launches += g.kernels;
+      return LB_KS_OK;
+    }
+  }
+  GraphEntry ge{};
+  ge.n = n;
+  ge.phase = h->phase;
+  ge.cur_in = h->cur;
+  LBKS_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int64_t nk = 0;
+  const int rc = issue_steps(h, n, h->cap_stream, &nk);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (ee != cudaSuccess) return cuda_fail(h, ee, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return cuda_fail(h, ie, "graph instantiate");
+  ge.cur_out = h->cur;
+  ge.kernels = nk;
+  ge.exec = exec;
+  if (h->graphs.size() >= 8) {
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(ge);
+  LBKS_CUDA(h, cudaGraphLaunch(exec, h->stream), "graph launch");
+  h->launches += nk;
+  return LB_KS_OK;
+}
+
+int check_flags(lb_ks* h) {
+  int flag = 0;
+  LBKS_CUDA(h, cudaMemcpy(&flag, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+  if (flag) {
+    h->sticky = LB_KS_EUNSTABLE;
+    return fail(h, LB_KS_EUNSTABLE, "non-finite FP64 mass at a guard step (the run went unstable)");
+  }
+  return LB_KS_OK;
+}
+
+int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const double* L, const double* dt,
+           const double* tau, const double* rho0, const lb_ks_opts* opts) {
+  if (!out) return fail(nullptr, LB_KS_EINVAL, "h must not be NULL");
+  *out = nullptr;
+  if (scheme != LB_KS_D1Q5 && scheme != LB_KS_D1Q7) return fail(nullptr, LB_KS_EINVAL, "scheme must be 5 or 7");
+  if (nruns < 1) return fail(nullptr, LB_KS_EINVAL, "nruns must be >= 1");
+  if (!N || !L || !dt || !tau || !rho0) return fail(nullptr, LB_KS_EINVAL, "NULL argument");
+  lb_ks_opts o;
+  lb_ks_default_opts(&o);
+  if (opts) o = *opts;
+  std::string why;
+  if (!valid_opts(o, &why)) return fail(nullptr, LB_KS_EINVAL, why);
+  const int cmax = (scheme - 1) / 2;
+  int64_t total = 0;
+  for (int32_t r = 0; r < nruns; ++r) {
+    if (N[r] < 2 * cmax + 1 || N[r] > (int64_t)1 << 30)
+      return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": N must be in [2 c_max + 1, 2^30]");
+    if (!(L[r] > 0.0) || !std::isfinite(L[r])) return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": L must be > 0");
+    if (!(dt[r] > 0.0) || !std::isfinite(dt[r])) return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": dt must be > 0");
+    if (!(tau[r] >= 1.0) || !std::isfinite(tau[r])) return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": tau must be >= 1");
+    total += N[r];
+  }
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(nullptr, LB_KS_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
+  }
+
+  lb_ks* h = new (std::nothrow) lb_ks();
+  if (!h) return fail(nullptr, LB_KS_ENOMEM, "host allocation failed");
+  auto bail = [&](int rc) {
+    g_ctor_error = h->err;
+    lb_ks_free(h);
+    return rc;
+  };
+  h->Q = scheme;
+  h->cmax = cmax;
+  h->prec = o.precision;
+  h->opts = o;
+  h->nruns = nruns;
+  h->stream = static_cast<cudaStream_t>(o.stream);
+  h->N.assign(N, N + nruns);
+  h->total_sites = total;
+
+  // Host copy of rho0 (host or device pointer): validation, mean, scale, mass.
+  std::vector<double> r0((size_t)total);
+  ce = cudaMemcpy(r0.data(), rho0, sizeof(double) * (size_t)total, cudaMemcpyDefault);
+  if (ce != cudaSuccess) { cudaGetLastError(); return bail(fail(h, LB_KS_EINVAL, std::string("cannot read rho0: ") + cudaGetErrorString(ce))); }
+  h->rho_off.resize(nruns + 1);
+  h->rho_off[0] = 0;
+  for (int32_t r = 0; r < nruns; ++r) h->rho_off[r + 1] = h->rho_off[r] + N[r];
+  h->runs_h.resize(nruns);
+  h->mass0_h.resize(nruns);
+  int64_t off = 0;
+  for (int32_t r = 0; r < nruns; ++r) {
+    RunDesc& d = h->runs_h[r];
+    std::memset(&d, 0, sizeof(d));
+    double A[7], B[7];
+    const double dx = L[r] / (double)N[r];
+    if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK)
+      return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
+    double mass = 0.0;
+    const double* rr = r0.data() + h->rho_off[r];
+    for (int64_t x = 0; x < N[r]; ++x) {
+      if (!std::isfinite(rr[x])) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": rho0 is not finite"));
+      mass += rr[x];
+    }
+    h->mass0_h[r] = mass;
+    const double rhobar = o.precision == kF64 ? 0.0 : mass / (double)N[r];
+    double gmax = 0.0;
+    if (o.precision == kF16S) {
+      for (int64_t x = 0; x < N[r]; ++x)
+        for (int i = 0; i < scheme; ++i) {
+          double v = A[i] * rr[x] + B[i] * rr[x] * rr[x] - (i == 0 ? rhobar : 0.0);
+          gmax = std::max(gmax, std::fabs(v));
+        }
+    }
+    const double scale = (o.precision == kF16S && gmax > 0.0) ? gmax : 1.0;
+    const double w = 1.0 / tau[r];
+    d.off = off;
+    d.N = N[r];
+    for (int i = 0; i < scheme; ++i) {
+      d.A[i] = A[i];
+      d.B[i] = B[i];
+      d.a[i] = A[i] * w;
+      d.b[i] = B[i] * w;
+      d.af[i] = (float)d.a[i];
+      d.bf[i] = (float)d.b[i];
+    }
+    d.r = 1.0 - w;
+    d.rhobar = rhobar;
+    d.d0 = -rhobar * w;
+    d.scale = scale;
+    d.inv_scale = 1.0 / scale;
+    d.rf = (float)d.r;
+    d.rhobarf = (float)d.rhobar;
+    d.d0f = (float)d.d0;
+    d.scalef = (float)scale;
+    d.inv_scalef = (float)(1.0 / scale);
+    off += align_up(N[r], kAlign);
+  }
+  h->plane = std::max<int64_t>(off, kAlign);
+
+  // Tiles.
+  std::vector<Tile> pt, st;
+  std::vector<int32_t> st_begin(nruns + 1);
+  const int TS = stream_tile_sites();
+  for (int32_t r = 0; r < nruns; ++r) {
+    for (int64_t x = 0; x < N[r]; x += kPlainTile) pt.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(kPlainTile, N[r] - x), 0});
+    st_begin[r] = (int32_t)st.size();
+    for (int64_t x = 0; x < N[r]; x += TS) st.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(TS, N[r] - x), 0});
+  }
+  st_begin[nruns] = (int32_t)st.size();
+  h->n_plain_tiles = (int)pt.size();
+  h->n_stream_tiles = (int)st.size();
+
+  int rc;
+  const size_t fbytes = storage_bytes(h->prec) * (size_t)scheme * (size_t)h->plane;
+  for (int b = 0; b < 2; ++b) {
+    unsigned char* p = nullptr;
+    if ((rc = dalloc(h, &p, fbytes))) return bail(rc);
+    h->fbuf[b] = p;
+    if ((ce = cudaMemset(p, 0, fbytes)) != cudaSuccess) return bail(cuda_fail(h, ce, "clear populations"));
+  }
+  if ((rc = dalloc(h, &h->d_runs, nruns))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_plain_tiles, pt.size()))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_stream_tiles, st.size()))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_stream_tile_begin, st_begin.size()))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_rho_off, h->rho_off.size()))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_stage, (size_t)total))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_partials, 2 * st.size()))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_mass0, nruns))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_mass, nruns))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_energy, nruns))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_delta, nruns))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_flags, 1))) return bail(rc);
+  auto up = [&](void* dst, const void* src, size_t bytes) { return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice); };
+  if ((ce = up(h->d_runs, h->runs_h.data(), sizeof(RunDesc) * nruns)) != cudaSuccess ||
+      (ce = up(h->d_plain_tiles, pt.data(), sizeof(Tile) * pt.size())) != cudaSuccess ||
+      (ce = up(h->d_stream_tiles, st.data(), sizeof(Tile) * st.size())) != cudaSuccess ||
+      (ce = up(h->d_stream_tile_begin, st_begin.data(), sizeof(int32_t) * st_begin.size())) != cudaSuccess ||
+      (ce = up(h->d_rho_off, h->rho_off.data(), sizeof(int64_t) * h->rho_off.size())) != cudaSuccess ||
+      (ce = up(h->d_mass0, h->mass0_h.data(), sizeof(double) * nruns)) != cudaSuccess ||
+      (ce = up(h->d_stage, r0.data(), sizeof(double) * (size_t)total)) != cudaSuccess ||
+      (ce = cudaMemset(h->d_flags, 0, sizeof(int))) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "upload"));
+
+  // Kernel family.
+  int kern = o.kernel;
+  if (kern == LB_KS_KERNEL_AUTO || kern == LB_KS_KERNEL_RESIDENT) {
+    rc = setup_resident(h, kern == LB_KS_KERNEL_RESIDENT);
+    if (rc < 0) return bail(rc);
+    kern = rc == 0 ? LB_KS_KERNEL_RESIDENT : (h->prec == kF64 ? LB_KS_KERNEL_PLAIN : LB_KS_KERNEL_STREAM);
+  }
+  h->kernel = kern;
+  if (kern == LB_KS_KERNEL_STREAM && (ce = stream_prepare(scheme, h->prec)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "stream kernel setup"));
+  if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "create capture stream"));
+
+  // f = f^eq(rho0).
+  if ((ce = launch_init_eq(scheme, h->prec, arena(h, 0), h->d_runs, h->d_stream_tiles, h->n_stream_tiles, h->d_stage,
+                           h->d_rho_off, h->stream)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "init"));
+  h->launches += 1;
+  if ((ce = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, ce, "init sync"));
+  *out = h;
+  return LB_KS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lb_ks_default_opts(lb_ks_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = LB_KS_F64;
+  o->dm_variant = LB_KS_DM_DERIVED;
+  o->recentre_every = 0;
+  o->kernel = LB_KS_KERNEL_AUTO;
+  o->use_graph = 1;
+  o->stream = nullptr;
+}
+
+int lb_ks_init(lb_ks_t** h, int scheme, int64_t N, double L, double dt, double tau, const double* rho0,
+               const lb_ks_opts* opts) {
+  return create(h, scheme, 1, &N, &L, &dt, &tau, rho0, opts);
+}
+
+int lb_ks_batch_init(lb_ks_t** h, int scheme, int32_t nruns, const int64_t* N, const double* L, const double* dt,
+                     const double* tau, const double* rho0, const lb_ks_opts* opts) {
+  return create(h, scheme, nruns, N, L, dt, tau, rho0, opts);
+}
+
+int lb_ks_step(lb_ks_t* h, int64_t n) {
+  if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
+  if (h->sticky) return h->sticky;
+  if (n < 0) return fail(h, LB_KS_EINVAL, "n must be >= 0");
+  const int64_t R = h->opts.recentre_every;
+  const int64_t chunk_max = h->kernel == LB_KS_KERNEL_RESIDENT ? 64LL * h->kmax : 512;
+  while (n > 0) {
+    int64_t c = std::min(n, chunk_max);
+    if (R > 0) c = std::min<int64_t>(c, R - h->phase);
+    int rc;
+    if (h->opts.use_graph) {
+      rc = run_chunk_graph(h, c);
+    } else {
+      int64_t nk = 0;
+      rc = issue_steps(h, c, h->stream, &nk);
+      h->launches += nk;
+    }
+    if (rc) return rc;
+    n -= c;
+  }
+  return LB_KS_OK;
+}
+
+int lb_ks_rho(lb_ks_t* h, double* out) {
+  if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
+  if (h->sticky) return h->sticky;
+  if (!out) return fail(h, LB_KS_EINVAL, "out must not be NULL");
+  LBKS_CUDA(h, launch_gather_rho(h->Q, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles, h->n_stream_tiles,
+                                 h->d_stage, h->d_rho_off, h->stream), "gather rho");
+  h->launches += 1;
+  LBKS_CUDA(h, cudaMemcpyAsync(out, h->d_stage, sizeof(double) * (size_t)h->total_sites, cudaMemcpyDefault, h->stream), "copy rho");
+  LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  return check_flags(h);
+}
+
+int lb_ks_mass_energy(lb_ks_t* h, double* mass, double* energy) {
+  if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
+  if (h->sticky) return h->sticky;
+  int64_t nk = 0;
+  int rc = issue_guard(h, h->stream, false, &nk);
+  if (rc) return rc;
+  h->launches += nk;
+  std::vector<double> m(h->nruns), e(h->nruns);
+  LBKS_CUDA(h, cudaMemcpyAsync(m.data(), h->d_mass, sizeof(double) * h->nruns, cudaMemcpyDeviceToHost, h->stream), "copy mass");
+  LBKS_CUDA(h, cudaMemcpyAsync(e.data(), h->d_energy, sizeof(double) * h->nruns, cudaMemcpyDeviceToHost, h->stream), "copy energy");
+  LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  if (mass) std::memcpy(mass, m.data(), sizeof(double) * h->nruns);
+  if (energy) std::memcpy(energy, e.data(), sizeof(double) * h->nruns);
+  return check_flags(h);
+}
+
+int lb_ks_state_bytes(const lb_ks_t* h, size_t* bytes) {
+  if (!h || !bytes) return LB_KS_EINVAL;
+  *bytes = 64 + sizeof(int64_t) * h->nruns + sizeof(RunDesc) * h->nruns + sizeof(double) * h->nruns +
+           storage_bytes(h->prec) * (size_t)h->Q * (size_t)h->plane;
+  return LB_KS_OK;
+}
+
+int lb_ks_save(lb_ks_t* h, void* buf, size_t bytes) {
+  if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
+  if (h->sticky) return h->sticky;
+  size_t need = 0;
+  lb_ks_state_bytes(h, &need);
+  if (!buf || bytes < need) return fail(h, LB_KS_EINVAL, "buffer too small for the checkpoint");
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  std::memset(p, 0, 64);
+  uint32_t hdr[6] = {kMagic, kVersion, (uint32_t)h->Q, (uint32_t)h->prec, (uint32_t)h->nruns, 0};
+  std::memcpy(p, hdr, sizeof(hdr));
+  int64_t hdr2[3] = {h->plane, h->steps_done, h->phase};
+  std::memcpy(p + 24, hdr2, sizeof(hdr2));
+  p += 64;
+  std::memcpy(p, h->N.data(), sizeof(int64_t) * h->nruns);
+  p += sizeof(int64_t) * h->nruns;
+  std::memcpy(p, h->runs_h.data(), sizeof(RunDesc) * h->nruns);
+  p += sizeof(RunDesc) * h->nruns;
+  std::memcpy(p, h->mass0_h.data(), sizeof(double) * h->nruns);
+  p += sizeof(double) * h->nruns;
+  LBKS_CUDA(h, cudaMemcpyAsync(p, h->fbuf[h->cur], storage_bytes(h->prec) * (size_t)h->Q * (size_t)h->plane,
+                               cudaMemcpyDeviceToHost, h->stream), "save");
+  LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  return check_flags(h);
+}
+
+int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
+  if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
+  size_t need = 0;
+  lb_ks_state_bytes(h, &need);
+  if (!buf || bytes < need) return fail(h, LB_KS_EINVAL, "checkpoint buffer too small");
+  const unsigned char* p = static_cast<const unsigned char*>(buf);
+  uint32_t hdr[6];
+  int64_t hdr2[3];
+  std::memcpy(hdr, p, sizeof(hdr));
+  std::memcpy(hdr2, p + 24, sizeof(hdr2));
+  if (hdr[0] != kMagic || hdr[1] != kVersion || hdr[2] != (uint32_t)h->Q || hdr[3] != (uint32_t)h->prec ||
+      hdr[4] != (uint32_t)h->nruns || hdr2[0] != h->plane)
+    return fail(h, LB_KS_EINVAL, "checkpoint does not match this handle (scheme, precision or runs)");
+  p += 64;
+  if (std::memcmp(p, h->N.data(), sizeof(int64_t) * h->nruns) != 0)
+    return fail(h, LB_KS_EINVAL, "checkpoint lattice sizes differ from this handle's");
+  p += sizeof(int64_t) * h->nruns;
+  std::vector<RunDesc> runs(h->nruns);
+  std::memcpy(runs.data(), p, sizeof(RunDesc) * h->nruns);
+  p += sizeof(RunDesc) * h->nruns;
+  std::vector<double> m0(h->nruns);
+  std::memcpy(m0.data(), p, sizeof(double) * h->nruns);
+  p += sizeof(double) * h->nruns;
+  LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+  h->runs_h = runs;
+  h->mass0_h = m0;
+  LBKS_CUDA(h, cudaMemcpy(h->d_runs, runs.data(), sizeof(RunDesc) * h->nruns, cudaMemcpyHostToDevice), "load runs");
+  LBKS_CUDA(h, cudaMemcpy(h->d_mass0, m0.data(), sizeof(double) * h->nruns, cudaMemcpyHostToDevice), "load mass0");
+  LBKS_CUDA(h, cudaMemcpy(h->fbuf[h->cur], p, storage_bytes(h->prec) * (size_t)h->Q * (size_t)h->plane,
+                          cudaMemcpyHostToDevice), "load populations");
+  h->steps_done = hdr2[1];
+  h->phase = hdr2[2];
+  h->sticky = LB_KS_OK;
+  LBKS_CUDA(h, cudaMemset(h->d_flags, 0, sizeof(int)), "clear flags");
+  return LB_KS_OK;
+}
+
+int64_t lb_ks_steps_done(const lb_ks_t* h) { return h ? h->steps_done : -1; }
+
+int lb_ks_describe(const lb_ks_t* h, int* kernel, int* spt, int* tpb, int* spl, int32_t* nruns, int64_t* total) {
+  if (!h) return LB_KS_EINVAL;
+  const bool res = h->kernel == LB_KS_KERNEL_RESIDENT;
+  if (kernel) *kernel = h->kernel;
+  if (spt) *spt = res ? h->S : 0;
+  if (tpb) *tpb = res ? h->NT : 0;
+  if (spl) *spl = res ? h->kmax : 0;
+  if (nruns) *nruns = h->nruns;
+  if (total) *total = h->total_sites;
+  return LB_KS_OK;
+}
+
+int64_t lb_ks_launches(const lb_ks_t* h) { return h ? h->launches : -1; }
+
+void lb_ks_free(lb_ks_t* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  cudaGetLastError();
+  delete h;
+}
+
+const char* lb_ks_last_error(const lb_ks_t* h) { return h ? h->err.c_str() : g_ctor_error.c_str(); }
+
+int lb_ks_fma_peak(int fp64, double* flops_per_s) {
+  if (!flops_per_s) return LB_KS_EINVAL;
+  cudaError_t e = fma_peak(fp64, flops_per_s, nullptr);
+  if (e != cudaSuccess) {
+    g_ctor_error = std::string("fma peak: ") + cudaGetErrorString(e);
+    return LB_KS_ECUDA;
+  }
+  return LB_KS_OK;
+}
+
+}  // extern "C"

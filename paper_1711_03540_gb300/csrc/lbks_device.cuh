@@ -1,0 +1,78 @@
+// Device-side building blocks shared by every kernel: lattice speeds,
+// storage conversion, and the fused collision of one site.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "lbks_internal.h"
+
+namespace lbks {
+
+// Lattice speeds c_i in the order 0, +1, -1, +2, -2, +3, -3 (Appendix A of the paper).
+__host__ __device__ constexpr int speed(int i) { return i == 0 ? 0 : ((i & 1) ? (i + 1) / 2 : -(i / 2)); }
+__host__ __device__ constexpr int cmax_of(int Q) { return (Q - 1) / 2; }
+
+template <int ST> struct StorageType;
+template <> struct StorageType<kF64> { using type = double; using compute = double; };
+template <> struct StorageType<kF32> { using type = float; using compute = float; };
+template <> struct StorageType<kF16S> { using type = __half; using compute = float; };
+
+// Per-run constants in the compute type.
+template <typename CT, int Q> struct Coef {
+  CT a[Q], b[Q];
+  CT r, rhobar, d0, scale, inv_scale;
+};
+
+template <typename CT, int Q>
+__device__ __forceinline__ Coef<CT, Q> load_coef(const RunDesc& d) {
+  Coef<CT, Q> c;
+  if constexpr (sizeof(CT) == 8) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) { c.a[i] = d.a[i]; c.b[i] = d.b[i]; }
+    c.r = d.r; c.rhobar = d.rhobar; c.d0 = d.d0; c.scale = d.scale; c.inv_scale = d.inv_scale;
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) { c.a[i] = d.af[i]; c.b[i] = d.bf[i]; }
+    c.r = d.rf; c.rhobar = d.rhobarf; c.d0 = d.d0f; c.scale = d.scalef; c.inv_scale = d.inv_scalef;
+  }
+  return c;
+}
+
+// Explicitly rounded arithmetic: no contraction choices are left to the compiler.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+__device__ __forceinline__ double to_compute(double v, double) { return v; }
+__device__ __forceinline__ float to_compute(float v, float) { return v; }
+__device__ __forceinline__ float to_compute(__half v, float scale) { return __fmul_rn(__half2float(v), scale); }
+
+__device__ __forceinline__ void from_compute(double v, double, double* p) { *p = v; }
+__device__ __forceinline__ void from_compute(float v, float, float* p) { *p = v; }
+__device__ __forceinline__ void from_compute(float v, float inv_scale, __half* p) {
+  *p = __float2half_rn(__fmul_rn(v, inv_scale));
+}
+
+// One site of Eq. LB_equation_ordinary in deviation form (see RunDesc):
+//   rho = rhobar + sum_i g_i;  g_i <- r g_i + rho (a_i + rho b_i);  g_0 also gets d0.
+// The summation order and the fma forms are fixed here so that every kernel
+// family produces bitwise the same post-collision values from the same inputs.
+template <int Q, typename CT>
+__device__ __forceinline__ void collide(CT (&g)[Q], const Coef<CT, Q>& k) {
+  CT rho = k.rhobar;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) rho = add_rn(rho, g[i]);
+  g[0] = fma_rn(k.r, g[0], fma_rn(rho, k.a[0], k.d0));  // b_0 = J w1_0 / tau = 0
+#pragma unroll
+  for (int i = 1; i < Q; ++i) g[i] = fma_rn(k.r, g[i], mul_rn(rho, fma_rn(rho, k.b[i], k.a[i])));
+}
+
+__device__ __forceinline__ int64_t wrap_site(int64_t x, int64_t N) {
+  return x < 0 ? x + N : (x >= N ? x - N : x);
+}
+
+}  // namespace lbks

@@ -1,0 +1,96 @@
+// Internal declarations shared by the host API and the kernel translation units.
+// Not part of the public ABI (that is include/lb_ks.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbks {
+
+constexpr int kMaxQ = 7;
+
+// Storage precisions (same values as LB_KS_F64 / LB_KS_F32 / LB_KS_F16S).
+enum Storage : int { kF64 = 0, kF32 = 1, kF16S = 2 };
+
+// Per-run constants, computed in FP64 on the host (lbks_params.cpp) and
+// uploaded once.  The step of Eq. LB_equation_ordinary is evaluated as
+//     rho  = rhobar + sum_i g_i                 (g_i = f_i - w0_i rhobar, the stored deviation)
+//     g*_i = r g_i + rho (a_i + rho b_i) + [i == 0] d0
+// with r = 1 - 1/tau, a_i = A_i / tau, b_i = B_i / tau, d0 = -rhobar / tau,
+// where f^eq_i = A_i rho + B_i rho^2.  For rhobar = 0 this is f*_i = f_i - (f_i - f^eq_i)/tau.
+struct RunDesc {
+  int64_t off;  // arena offset (elements) of site 0 of this run in every plane
+  int64_t N;    // sites
+  double a[8], b[8];  // A_i / tau, B_i / tau
+  double A[8], B[8];  // equilibrium coefficients
+  double r, rhobar, d0, scale, inv_scale;  // scale: F16S stored value = g / scale
+  float af[8], bf[8];
+  float rf, rhobarf, d0f, scalef, inv_scalef;
+  int32_t pad[3];
+};
+
+// One unit of work of the resident kernel: a lattice (ring) or a stretch of
+// one (segment) held by a range of threads of one thread block.
+struct Piece {
+  int32_t run;
+  int32_t t0;     // first thread of the block
+  int32_t nthr;   // threads V; thread j holds S or S-1 consecutive sites
+  int32_t n;      // sites loaded (ring: N)
+  int64_t x0;     // run-local site of loaded index 0, in [0, N)
+  int32_t st_lo;  // loaded indices [st_lo, st_hi) are written back
+  int32_t st_hi;
+};
+
+// Tile of the one-thread-per-site and streaming kernels: sites [x0, x0 + len) of one run.
+struct Tile {
+  int32_t run;
+  int32_t x0;
+  int32_t len;
+  int32_t pad;
+};
+
+struct Arena {
+  void* f;        // plane i of run r at element i * plane + runs[r].off
+  int64_t plane;  // plane stride (elements)
+};
+
+// ---- launchers (each returns the CUDA error of the launch) ----
+cudaError_t launch_init_eq(int Q, int storage, Arena dst, const RunDesc* runs, const Tile* tiles,
+                           int ntiles, const double* rho0, const int64_t* rho_off, cudaStream_t s);
+cudaError_t launch_gather_rho(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles,
+                              int ntiles, double* out, const int64_t* out_off, cudaStream_t s);
+cudaError_t launch_plain_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
+                              const Tile* tiles, int ntiles, cudaStream_t s);
+cudaError_t launch_stream_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
+                               const Tile* tiles, int ntiles, cudaStream_t s);
+// Guard: per-tile FP64 partial sums of rho and rho^2 (scratch: 2 doubles per tile),
+// then per-run totals, non-finite flag, and (if recentre) g_0 += (M0 - M)/N.
+cudaError_t launch_mass_partials(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles,
+                                 int ntiles, double* partials, cudaStream_t s);
+cudaError_t launch_mass_finalize(int nruns, const int32_t* tile_begin, const double* partials,
+                                 const RunDesc* runs, const double* mass0, double* mass, double* energy,
+                                 double* delta, int* flags, cudaStream_t s);
+cudaError_t launch_recentre(int storage, Arena f, const RunDesc* runs, const Tile* tiles, int ntiles,
+                            const double* delta, cudaStream_t s);
+
+struct ResidentLaunch {
+  int Q, storage, S, NT;
+  Arena src, dst;
+  const RunDesc* runs;
+  const Piece* pieces;
+  const int2* bundles;  // (first piece, piece count) per bundle
+  int nbundles;
+  int* queue;           // work counter, zeroed before each launch
+  int ksteps;
+  int grid;
+};
+bool resident_supported(int Q, int storage, int S, int NT);
+cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm);
+size_t resident_smem_bytes(int Q, int storage, int NT);
+cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
+
+// Diagnostic micro-benchmark of the FMA pipes (flop/s), used by the benchmark
+// to state measured ALU peaks beside the derived ones.
+cudaError_t fma_peak(int fp64, double* flops_per_s, cudaStream_t s);
+
+}  // namespace lbks

@@ -1,0 +1,269 @@
+// One-thread-per-site kernels: initialisation at equilibrium, the plain
+// fused step (the FP64 baseline), the rho gather and the FP64 mass guard.
+#include "lbks_device.cuh"
+
+namespace lbks {
+
+namespace {
+
+constexpr int kPlainThreads = 256;
+
+// f_i = f^eq_i(rho0) = A_i rho0 + B_i rho0^2 (Sec. 2, Eq. feq and its D1Q7 form),
+// evaluated in FP64 and stored as the deviation g_i = f_i - w0_i rhobar.
+template <int Q, int ST>
+__global__ void __launch_bounds__(kPlainThreads) init_eq_kernel(Arena dst, const RunDesc* __restrict__ runs,
+                                                                const Tile* __restrict__ tiles,
+                                                                const double* __restrict__ rho0,
+                                                                const int64_t* __restrict__ rho_off) {
+  using T = typename StorageType<ST>::type;
+  using CT = typename StorageType<ST>::compute;
+  const Tile tl = tiles[blockIdx.x];
+  const RunDesc& d = runs[tl.run];
+  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+    const int64_t x = tl.x0 + k;
+    const double rho = rho0[rho_off[tl.run] + x];
+    T* f = static_cast<T*>(dst.f) + d.off + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double v = __fma_rn(d.B[i], __dmul_rn(rho, rho), __dmul_rn(d.A[i], rho));
+      if (i == 0) v = __dsub_rn(v, d.rhobar);
+      from_compute(static_cast<CT>(v), static_cast<CT>(d.inv_scale), f + (int64_t)i * dst.plane);
+    }
+  }
+}
+
+// rho = rhobar + sum_i g_i, accumulated in FP64.
+template <int Q, int ST>
+__global__ void __launch_bounds__(kPlainThreads) gather_rho_kernel(Arena src, const RunDesc* __restrict__ runs,
+                                                                   const Tile* __restrict__ tiles,
+                                                                   double* __restrict__ out,
+                                                                   const int64_t* __restrict__ out_off) {
+  using T = typename StorageType<ST>::type;
+  using CT = typename StorageType<ST>::compute;
+  const Tile tl = tiles[blockIdx.x];
+  const RunDesc& d = runs[tl.run];
+  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+    const int64_t x = tl.x0 + k;
+    const T* f = static_cast<const T*>(src.f) + d.off + x;
+    double rho = d.rhobar;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += static_cast<double>(to_compute(f[(int64_t)i * src.plane], static_cast<CT>(d.scale)));
+    out[out_off[tl.run] + x] = rho;
+  }
+}
+
+// The plain fused step: one thread per site reads its Q populations, collides
+// (Eq. LB_equation_ordinary) and pushes f*_i to site x + c_i (mod N).
+template <int Q, int ST>
+__global__ void __launch_bounds__(kPlainThreads) plain_step_kernel(Arena src, Arena dst,
+                                                                   const RunDesc* __restrict__ runs,
+                                                                   const Tile* __restrict__ tiles) {
+  using T = typename StorageType<ST>::type;
+  using CT = typename StorageType<ST>::compute;
+  const Tile tl = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= tl.len) return;
+  const RunDesc& d = runs[tl.run];
+  const Coef<CT, Q> k = load_coef<CT, Q>(d);
+  const int64_t x = tl.x0 + threadIdx.x;
+  const T* fs = static_cast<const T*>(src.f) + d.off;
+  T* fd = static_cast<T*>(dst.f) + d.off;
+  CT g[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) g[i] = to_compute(fs[(int64_t)i * src.plane + x], k.scale);
+  collide<Q, CT>(g, k);
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    from_compute(g[i], k.inv_scale, fd + (int64_t)i * dst.plane + wrap_site(x + speed(i), d.N));
+}
+
+// Guard, pass 1: FP64 sums of rho and rho^2 over one tile (fixed-order tree).
+template <int Q, int ST>
+__global__ void __launch_bounds__(kPlainThreads) mass_partials_kernel(Arena src, const RunDesc* __restrict__ runs,
+                                                                      const Tile* __restrict__ tiles,
+                                                                      double* __restrict__ partials) {
+  using T = typename StorageType<ST>::type;
+  using CT = typename StorageType<ST>::compute;
+  const Tile tl = tiles[blockIdx.x];
+  const RunDesc& d = runs[tl.run];
+  double m = 0.0, e = 0.0;
+  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+    const T* f = static_cast<const T*>(src.f) + d.off + tl.x0 + k;
+    double rho = d.rhobar;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += static_cast<double>(to_compute(f[(int64_t)i * src.plane], static_cast<CT>(d.scale)));
+    m += rho;
+    e = __fma_rn(rho, rho, e);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+  }
+  __shared__ double sm[2][kPlainThreads / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sm[0][w] = m; sm[1][w] = e; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0, ee = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { mm += sm[0][i]; ee += sm[1][i]; }
+    partials[2 * blockIdx.x] = mm;
+    partials[2 * blockIdx.x + 1] = ee;
+  }
+}
+
+// Guard, pass 2: one warp per run sums that run's tile partials in a fixed
+// order, flags a non-finite mass, and computes the re-centring increment
+// (M0 - M)/N for g_0 (the mass invariant: sum_i f^eq_i = rho, Eq. cond_weight).
+__global__ void mass_finalize_kernel(int nruns, const int32_t* __restrict__ tile_begin,
+                                     const double* __restrict__ partials, const RunDesc* __restrict__ runs,
+                                     const double* __restrict__ mass0, double* __restrict__ mass,
+                                     double* __restrict__ energy, double* __restrict__ delta, int* __restrict__ flags) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nruns) return;
+  double m = 0.0, e = 0.0;
+  for (int t = tile_begin[warp] + lane; t < tile_begin[warp + 1]; t += 32) {
+    m += partials[2 * t];
+    e += partials[2 * t + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+  }
+  if (lane == 0) {
+    if (mass) mass[warp] = m;
+    if (energy) energy[warp] = e;
+    const bool ok = isfinite(m) && isfinite(e);
+    if (!ok) atomicOr(flags, 1);
+    if (delta) delta[warp] = ok ? (mass0[warp] - m) / static_cast<double>(runs[warp].N) : 0.0;
+  }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kPlainThreads) recentre_kernel(Arena f, const RunDesc* __restrict__ runs,
+                                                                 const Tile* __restrict__ tiles,
+                                                                 const double* __restrict__ delta) {
+  using T = typename StorageType<ST>::type;
+  using CT = typename StorageType<ST>::compute;
+  const Tile tl = tiles[blockIdx.x];
+  const RunDesc& d = runs[tl.run];
+  const double dl = delta[tl.run];
+  if (dl == 0.0) return;
+  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+    T* p = static_cast<T*>(f.f) + d.off + tl.x0 + k;
+    const double v = static_cast<double>(to_compute(*p, static_cast<CT>(d.scale))) + dl;
+    from_compute(static_cast<CT>(v), static_cast<CT>(d.inv_scale), p);
+  }
+}
+
+// FMA-pipe micro-benchmark: independent chains of fused multiply-adds.
+template <typename T>
+__global__ void fma_peak_kernel(T* out, int iters, T seed) {
+  T a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  const T m = (T)0.999999, c = (T)1e-7;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a0 = fma_rn(a0, m, c); a1 = fma_rn(a1, m, c); a2 = fma_rn(a2, m, c); a3 = fma_rn(a3, m, c);
+      a4 = fma_rn(a4, m, c); a5 = fma_rn(a5, m, c); a6 = fma_rn(a6, m, c); a7 = fma_rn(a7, m, c);
+    }
+  }
+  const T s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == (T)-1.2345) out[threadIdx.x] = s;  // keeps the chains alive
+}
+
+}  // namespace
+
+#define LBKS_DISPATCH_Q_ST(Q, ST, CALL)                                     \
+  do {                                                                      \
+    if ((Q) == 5 && (ST) == kF64) { constexpr int Qc = 5, STc = kF64; CALL; } \
+    else if ((Q) == 5 && (ST) == kF32) { constexpr int Qc = 5, STc = kF32; CALL; } \
+    else if ((Q) == 5 && (ST) == kF16S) { constexpr int Qc = 5, STc = kF16S; CALL; } \
+    else if ((Q) == 7 && (ST) == kF64) { constexpr int Qc = 7, STc = kF64; CALL; } \
+    else if ((Q) == 7 && (ST) == kF32) { constexpr int Qc = 7, STc = kF32; CALL; } \
+    else if ((Q) == 7 && (ST) == kF16S) { constexpr int Qc = 7, STc = kF16S; CALL; } \
+    else return cudaErrorInvalidValue;                                      \
+  } while (0)
+
+cudaError_t launch_init_eq(int Q, int storage, Arena dst, const RunDesc* runs, const Tile* tiles, int ntiles,
+                           const double* rho0, const int64_t* rho_off, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  LBKS_DISPATCH_Q_ST(Q, storage, (init_eq_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(dst, runs, tiles, rho0, rho_off)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rho(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles, int ntiles,
+                              double* out, const int64_t* out_off, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  LBKS_DISPATCH_Q_ST(Q, storage, (gather_rho_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, out, out_off)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
+                              int ntiles, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  if (storage == kF16S) return cudaErrorInvalidValue;
+  LBKS_DISPATCH_Q_ST(Q, storage, (plain_step_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, dst, runs, tiles)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_partials(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles, int ntiles,
+                                 double* partials, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  LBKS_DISPATCH_Q_ST(Q, storage, (mass_partials_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, partials)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_finalize(int nruns, const int32_t* tile_begin, const double* partials, const RunDesc* runs,
+                                 const double* mass0, double* mass, double* energy, double* delta, int* flags,
+                                 cudaStream_t s) {
+  if (nruns == 0) return cudaSuccess;
+  const int threads = 128;
+  const int blocks = (nruns * 32 + threads - 1) / threads;
+  mass_finalize_kernel<<<blocks, threads, 0, s>>>(nruns, tile_begin, partials, runs, mass0, mass, energy, delta, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recentre(int storage, Arena f, const RunDesc* runs, const Tile* tiles, int ntiles,
+                            const double* delta, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  if (storage == kF64) recentre_kernel<kF64><<<ntiles, kPlainThreads, 0, s>>>(f, runs, tiles, delta);
+  else if (storage == kF32) recentre_kernel<kF32><<<ntiles, kPlainThreads, 0, s>>>(f, runs, tiles, delta);
+  else if (storage == kF16S) recentre_kernel<kF16S><<<ntiles, kPlainThreads, 0, s>>>(f, runs, tiles, delta);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t fma_peak(int fp64, double* flops_per_s, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  void* out = nullptr;
+  e = cudaMalloc(&out, 1024 * sizeof(double));
+  if (e != cudaSuccess) return e;
+  const int threads = 1024, blocks = sms * 2;
+  const int iters = fp64 ? 256 : 8192;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  for (int rep = 0; rep < 2; ++rep) {  // first pass warms up
+    cudaEventRecord(t0, s);
+    if (fp64) fma_peak_kernel<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.5);
+    else fma_peak_kernel<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.5f);
+    cudaEventRecord(t1, s);
+  }
+  e = cudaEventSynchronize(t1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+  if (e == cudaSuccess) *flops_per_s = 2.0 * 8.0 * 8.0 * iters * (double)threads * blocks / (ms * 1e-3);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFree(out);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+}  // namespace lbks

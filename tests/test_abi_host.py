@@ -1,0 +1,108 @@
+"""CPU tests of the C ABI: the library loads and exports every entry point
+declared in include/lb_ks.h, the host-side precompute matches the oracle,
+and argument validation fails cleanly (no GPU needed)."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lb():
+    from paper_1711_03540_gb300 import build
+
+    build.build()
+    import paper_1711_03540_gb300 as lb
+
+    return lb
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lb_ks.h")).read()
+    return sorted(set(re.findall(r"LB_KS_API[^;(]*?\b(lb_ks_\w+)\s*\(", txt)))
+
+
+def test_header_declarations_exported(lb):
+    import ctypes
+
+    names = _declared()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(lb.library_path())
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in lb_ks.h but not exported"
+    assert sorted(lb.ABI_FUNCTIONS) == names  # the binding wraps exactly the declared ABI
+
+
+@pytest.mark.parametrize("Q", [5, 7])
+@pytest.mark.parametrize("alpha,beta,tau", [(0.1, 1e-4, 1.0), (0.2, 1e-3, 1.5), (0.0245, 5e-6, 3.0)])
+@pytest.mark.parametrize("dmv", [0, 1])
+def test_params_match_oracle(lb, Q, alpha, beta, tau, dmv):
+    from oracle import lbks as ora
+
+    A, B, coef = lb.lb_ks_params(Q, alpha, beta, tau, dmv)
+    Ao, Bo = ora.feq_linear_quadratic(Q, alpha, beta, tau, dmv)
+    np.testing.assert_allclose(A, Ao, rtol=1e-13, atol=1e-15)
+    co = ora.coefficients(Q, alpha, beta, tau, dmv)
+    # (feq(1) + feq(-1))/2 loses digits to cancellation; the oracle's J w1 does not
+    np.testing.assert_allclose(B, co["J"] * ora.weight(Q, 1), rtol=1e-14, atol=0)
+    np.testing.assert_allclose(B, Bo, rtol=0, atol=1e-14 * np.abs(Ao).max())
+    np.testing.assert_allclose(coef, [co[k] for k in ["T1", "T2", "T3", "T4", "J", "K", "M", "dM", "E"]],
+                               rtol=1e-13, atol=1e-300)
+    # the equilibrium carries the mass: sum_i A_i = 1, sum_i B_i = 0
+    assert abs(A.sum() - 1.0) < 1e-12 * max(1.0, np.abs(A).max())
+    assert abs(B.sum()) < 1e-15
+
+
+def test_params_reject_invalid(lb):
+    for args in [(6, 0.1, 1e-4, 1.0), (7, 0.0, 1e-4, 1.0), (7, 0.1, -1.0, 1.0), (7, 0.1, 1e-4, 0.5),
+                 (7, 0.1, 1e-4, math.nan)]:
+        with pytest.raises(lb.LbKsError) as e:
+            lb.lb_ks_params(*args)
+        assert e.value.code == -1
+
+
+def test_tau_fit_matches_oracle_and_paper(lb):
+    from oracle import analysis
+
+    for Q in (5, 7):
+        for dX in (0.05, 0.1, 0.2):
+            for dT in (1e-7, 1e-6, 1e-5, 1e-4, 1e-3):
+                assert lb.lb_ks_tau_fit(Q, dX, dT) == pytest.approx(analysis.tau_fit(Q, dX, dT), rel=1e-13)
+    assert lb.lb_ks_tau_fit(7, 0.1, 1e-4) == pytest.approx(1.5076, abs=1e-3)
+    assert math.isnan(lb.lb_ks_tau_fit(4, 0.1, 1e-4))
+
+
+@pytest.mark.parametrize("bad", [
+    dict(scheme=6), dict(N=6), dict(L=0.0), dict(dt=-1e-4), dict(tau=0.95), dict(rho_nan=True),
+    dict(opts=dict(precision=3)), dict(opts=dict(kernel=7)), dict(opts=dict(sites_per_thread=5)),
+    dict(opts=dict(kernel=1, precision=2)), dict(opts=dict(threads_per_block=48)),
+])
+def test_init_rejects_invalid_arguments(lb, bad):
+    """Validation happens on the host before any device work: EINVAL on any
+    machine (with or without a GPU), with a reason, and no handle."""
+    args = dict(scheme=7, N=64, L=6.4, dt=1e-4, tau=1.5)
+    args.update({k: v for k, v in bad.items() if k in args})
+    rho0 = np.zeros(max(args["N"], 1))
+    if bad.get("rho_nan"):
+        rho0[3] = np.nan
+    opts = lb.lb_ks_default_opts(**bad.get("opts", {}))
+    with pytest.raises(lb.LbKsError) as e:
+        lb.lb_ks_init(args["scheme"], args["N"], args["L"], args["dt"], args["tau"], rho0, opts)
+    if bad.get("rho_nan"):
+        assert e.value.code in (-1, -3)  # rho0 is read after the device check
+    else:
+        assert e.value.code == -1
+    assert lb.lb_ks_last_error(None) not in ("", "no error")
+
+
+def test_no_device_is_an_error_not_a_fallback(lb):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lb.LbKsError) as e:
+        lb.lb_ks_init(7, 64, 6.4, 1e-4, 1.5, np.zeros(64))
+    assert e.value.code == -3

@@ -1,0 +1,241 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances:
+ * FP64 (all kernel families): max |rho_GPU - rho_oracle| <= 1e-12 after 1000
+   steps of the 512-site two-harmonic workload (the bar the method's FP64
+   implementation is held to); elsewhere 1e-12 relative to max |rho|.
+ * The three kernel families run the same fused arithmetic, so with equal
+   storage precision they agree bitwise.
+ * FP32: each step rounds Q populations (~Q * 2^-24 relative), a random walk
+   over n steps: the tests bound rel-L2 by 2e-6 * sqrt(n / 1000) * growth,
+   with growth the linear amplification exp(T/4) of KS (T = n dt).
+"""
+import numpy as np
+import pytest
+
+from oracle import lbks as ora
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L32 = 32 * np.pi
+
+
+@pytest.fixture(scope="module")
+def lb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_03540_gb300 import build
+
+    build.build()
+    import paper_1711_03540_gb300 as lb
+
+    return lb
+
+
+def run_gpu(lb, Q, N, L, dt, tau, rho0, n, **opts):
+    N = np.atleast_1d(np.asarray(N, dtype=np.int64))
+    L = np.broadcast_to(np.asarray(L, dtype=np.float64), N.shape).copy()
+    dt = np.broadcast_to(np.asarray(dt, dtype=np.float64), N.shape).copy()
+    tau = np.broadcast_to(np.asarray(tau, dtype=np.float64), N.shape).copy()
+    h = lb.lb_ks_batch_init(Q, N, L, dt, tau, np.ascontiguousarray(rho0, dtype=np.float64), lb.lb_ks_default_opts(**opts))
+    try:
+        lb.lb_ks_step(h, n)
+        out = np.empty(int(N.sum()))
+        lb.lb_ks_rho(h, out)
+        desc = lb.lb_ks_describe(h)
+    finally:
+        lb.lb_ks_free(h)
+    return out, desc
+
+
+def two_harmonic(N, L=L32):
+    X = np.arange(N) * (L / N)
+    return np.cos(X / 16) * (1 + np.sin(X / 16))
+
+
+KERNELS = {"plain": 1, "stream": 2, "resident": 3}
+
+
+@pytest.mark.parametrize("kern", ["plain", "stream", "resident"])
+def test_fp64_512_sites_1000_steps_matches_oracle(lb, kern):
+    N, dt, tau = 512, 5e-5, 1.0
+    r0 = two_harmonic(N)
+    ref = ora.run(5, r0, L32 / N, dt, tau, 1000)
+    out, desc = run_gpu(lb, 5, N, L32, dt, tau, r0, 1000, kernel=KERNELS[kern])
+    assert desc["kernel"] == KERNELS[kern]
+    assert np.max(np.abs(out - ref)) <= 1e-12
+    assert abs(out.sum() - r0.sum()) <= 1e-12 * np.abs(r0).sum()
+
+
+@pytest.mark.parametrize("Q", [5, 7])
+@pytest.mark.parametrize("kern,S,NT", [("plain", 0, 0), ("stream", 0, 0), ("resident", 8, 256), ("resident", 4, 64),
+                                       ("resident", 6, 96)])
+def test_fp64_ragged_batch_matches_oracle(lb, Q, kern, S, NT):
+    """Uneven lattice lengths (primes, the minimum 2 c_max + 1, tile edges, and
+    lengths that force the resident kernel to split lattices into segments)."""
+    cm = (Q - 1) // 2
+    Ns = np.array([2 * cm + 1, 13, 97, 255, 256, 257, 1023, 1025, 2049, 3001], dtype=np.int64)
+    rng = np.random.default_rng(11)
+    r0 = np.concatenate([0.3 * rng.standard_normal(n) + 0.1 for n in Ns])
+    dx = np.linspace(0.3, 0.6, Ns.size)
+    Ls = Ns * dx
+    dts = np.full(Ns.size, 2e-4)
+    taus = np.linspace(1.0, 2.0, Ns.size)
+    n = 300
+    ref, _ = ora.run_batch(Q, Ns, dx, dts, taus, r0, n)
+    out, desc = run_gpu(lb, Q, Ns, Ls, dts, taus, r0, n, kernel=KERNELS[kern], sites_per_thread=S,
+                        threads_per_block=NT, steps_per_launch=37 if kern == "resident" else 0)
+    assert desc["kernel"] == KERNELS[kern]
+    assert np.max(np.abs(out - ref)) <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kernel_families_agree_bitwise(lb, prec):
+    Ns = np.array([300, 777, 1500, 5000], dtype=np.int64)
+    rng = np.random.default_rng(3)
+    r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
+    args = (7, Ns, Ns * 0.1, np.full(4, 1e-4), np.array([1.5, 2.0, 2.5, 3.0]), r0, 200)
+    outs = [run_gpu(lb, *args, precision=prec, kernel=k)[0] for k in (1, 2, 3)]
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    seg = run_gpu(lb, *args, precision=prec, kernel=3, threads_per_block=64, steps_per_launch=16)[0]
+    np.testing.assert_array_equal(outs[0], seg)
+
+
+def test_f16s_resident_one_step_per_launch_equals_stream(lb):
+    Ns = np.array([640, 2000], dtype=np.int64)
+    rng = np.random.default_rng(4)
+    r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
+    args = (7, Ns, Ns * 0.1, np.full(2, 1e-4), np.array([1.5, 2.5]), r0, 50)
+    a = run_gpu(lb, *args, precision=2, kernel=2)[0]
+    b = run_gpu(lb, *args, precision=2, kernel=3, steps_per_launch=1)[0]
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("kern", [2, 3])
+def test_fp32_error_against_oracle(lb, kern):
+    Ns = np.array([256, 1000, 4000, 8192], dtype=np.int64)
+    from paper_1711_03540_gb300 import workloads
+
+    rng = np.random.default_rng(5)
+    r0 = np.concatenate([workloads.random_modes(int(n), n * 0.1, rng) for n in Ns])
+    taus = np.array([1.5, 2.0, 2.5, 3.0])
+    n, dt = 2000, 1e-4
+    ref, _ = ora.run_batch(7, Ns, np.full(4, 0.1), np.full(4, dt), taus, r0, n)
+    out, _ = run_gpu(lb, 7, Ns, Ns * 0.1, dt, taus, r0, n, precision=1, kernel=kern, recentre_every=500)
+    rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-6 * np.sqrt(n / 1000) * np.exp(n * dt / 4)
+
+
+def test_zero_steps_returns_initial_density(lb):
+    r0 = two_harmonic(100)
+    for prec in (0, 1):
+        out, _ = run_gpu(lb, 7, 100, 10.0, 1e-4, 1.5, r0, 0, precision=prec)
+        assert np.max(np.abs(out - r0)) <= (1e-14 if prec == 0 else 1e-6)
+
+
+def test_split_calls_equal_one_call_and_graph_replay(lb):
+    Ns = np.array([500, 3000], dtype=np.int64)
+    rng = np.random.default_rng(8)
+    r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
+    base = dict(precision=1, recentre_every=64)
+    for kern in (2, 3):
+        h1 = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(2, 1e-4), np.array([2.0, 2.5]), r0,
+                                 lb.lb_ks_default_opts(kernel=kern, **base))
+        h2 = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(2, 1e-4), np.array([2.0, 2.5]), r0,
+                                 lb.lb_ks_default_opts(kernel=kern, use_graph=0, **base))
+        try:
+            for _ in range(5):
+                lb.lb_ks_step(h1, 100)  # graphs replayed after the first capture
+            for _ in range(10):
+                lb.lb_ks_step(h2, 50)
+            a, b = np.empty(r0.size), np.empty(r0.size)
+            lb.lb_ks_rho(h1, a)
+            lb.lb_ks_rho(h2, b)
+            assert lb.lb_ks_steps_done(h1) == lb.lb_ks_steps_done(h2) == 500
+        finally:
+            lb.lb_ks_free(h1)
+            lb.lb_ks_free(h2)
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_checkpoint_resume_bitwise(lb, prec):
+    Ns = np.array([700, 2500], dtype=np.int64)
+    rng = np.random.default_rng(9)
+    r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
+    mk = lambda: lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(2, 1e-4), np.array([1.7, 2.9]), r0,
+                                     lb.lb_ks_default_opts(precision=prec, recentre_every=100 if prec else 0))
+    a, b = mk(), mk()
+    try:
+        lb.lb_ks_step(a, 1000)
+        lb.lb_ks_step(b, 500)
+        buf = np.zeros(lb.lb_ks_state_bytes(b), dtype=np.uint8)
+        lb.lb_ks_save(b, buf)
+        lb.lb_ks_free(b)
+        b = mk()
+        lb.lb_ks_load(b, buf)
+        assert lb.lb_ks_steps_done(b) == 500
+        lb.lb_ks_step(b, 500)
+        ra, rb = np.empty(r0.size), np.empty(r0.size)
+        lb.lb_ks_rho(a, ra)
+        lb.lb_ks_rho(b, rb)
+    finally:
+        lb.lb_ks_free(a)
+        lb.lb_ks_free(b)
+    np.testing.assert_array_equal(ra, rb)
+
+
+def test_recentring_holds_the_mass(lb):
+    """The FP64 guard returns every run's mass to its initial value (the
+    invariant sum_i f^eq_i = rho) after each recentring."""
+    Ns = np.array([1000, 3000, 6000], dtype=np.int64)
+    rng = np.random.default_rng(12)
+    r0 = np.concatenate([0.5 + 0.01 * rng.standard_normal(n) for n in Ns])
+    m0 = np.array([r0[:1000].sum(), r0[1000:4000].sum(), r0[4000:].sum()])
+    for prec in (1, 2):
+        h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(3, 1e-4), np.array([1.5, 2.0, 3.0]), r0,
+                                lb.lb_ks_default_opts(precision=prec, recentre_every=250))
+        try:
+            lb.lb_ks_step(h, 2000)
+            m, e = np.empty(3), np.empty(3)
+            lb.lb_ks_mass_energy(h, m, e)
+        finally:
+            lb.lb_ks_free(h)
+        tol = 1e-9 if prec == 1 else 1e-4
+        assert np.all(np.abs(m - m0) <= tol * np.abs(m0))
+        assert np.all(e > 0)
+
+
+def test_device_pointers_and_torch_stream(lb):
+    N = 2048
+    r0 = torch.tensor(two_harmonic(N, 204.8), dtype=torch.float64, device="cuda")
+    out = torch.empty(N, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    h = lb.lb_ks_init(7, N, 204.8, 1e-4, 1.5, r0, lb.lb_ks_default_opts(stream=s))
+    try:
+        lb.lb_ks_step(h, 200)
+        lb.lb_ks_rho(h, out)
+    finally:
+        lb.lb_ks_free(h)
+    ref = ora.run(7, r0.cpu().numpy(), 0.1, 1e-4, 1.5, 200)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_unstable_run_is_reported_and_sticky(lb):
+    """A time step far beyond the stability limit blows up; the FP64 guard sees a
+    non-finite mass, and the handle then reports LB_KS_EUNSTABLE on every call."""
+    N = 256
+    r0 = 0.5 * np.cos(2 * np.pi * 7 * np.arange(N) / N)
+    h = lb.lb_ks_init(5, N, N * 0.05, 5e-2, 1.0, r0, lb.lb_ks_default_opts(precision=1, recentre_every=50))
+    try:
+        lb.lb_ks_step(h, 5000)
+        with pytest.raises(lb.LbKsError) as e:
+            lb.lb_ks_rho(h, np.empty(N))
+        assert e.value.code == -4
+        with pytest.raises(lb.LbKsError) as e:
+            lb.lb_ks_step(h, 1)
+        assert e.value.code == -4
+    finally:
+        lb.lb_ks_free(h)
