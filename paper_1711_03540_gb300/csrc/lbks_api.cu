@@ -452,12 +452,10 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     }
     d.r = 1.0 - w;
     d.rhobar = rhobar;
-    d.d0 = -rhobar * w;
     d.scale = scale;
     d.inv_scale = 1.0 / scale;
     d.rf = (float)d.r;
     d.rhobarf = (float)d.rhobar;
-    d.d0f = (float)d.d0;
     d.scalef = (float)scale;
     d.inv_scalef = (float)(1.0 / scale);
     off += align_up(N[r], kAlign);

@@ -15,18 +15,18 @@ enum Storage : int { kF64 = 0, kF32 = 1, kF16S = 2 };
 // Per-run constants, computed in FP64 on the host (lbks_params.cpp) and
 // uploaded once.  The step of Eq. LB_equation_ordinary is evaluated as
 //     rho  = rhobar + sum_i g_i                 (g_i = f_i - w0_i rhobar, the stored deviation)
-//     g*_i = r g_i + rho (a_i + rho b_i) + [i == 0] d0
-// with r = 1 - 1/tau, a_i = A_i / tau, b_i = B_i / tau, d0 = -rhobar / tau,
-// where f^eq_i = A_i rho + B_i rho^2.  For rhobar = 0 this is f*_i = f_i - (f_i - f^eq_i)/tau.
+//     g*_i = r g_i + rho a_i + rho^2 b_i        (i >= 1)
+//     g*_0 = sum_i g_i - sum_{i>=1} g*_i        (mass conservation of the collision)
+// with r = 1 - 1/tau, a_i = A_i / tau, b_i = B_i / tau, where f^eq_i = A_i rho + B_i rho^2.
+// For rhobar = 0 this is f*_i = f_i - (f_i - f^eq_i)/tau.
 struct RunDesc {
   int64_t off;  // arena offset (elements) of site 0 of this run in every plane
   int64_t N;    // sites
   double a[8], b[8];  // A_i / tau, B_i / tau
   double A[8], B[8];  // equilibrium coefficients
-  double r, rhobar, d0, scale, inv_scale;  // scale: F16S stored value = g / scale
+  double r, rhobar, scale, inv_scale;  // scale: F16S stored value = g / scale
   float af[8], bf[8];
-  float rf, rhobarf, d0f, scalef, inv_scalef;
-  int32_t pad[3];
+  float rf, rhobarf, scalef, inv_scalef;
 };
 
 // One unit of work of the resident kernel: a lattice (ring) or a stretch of

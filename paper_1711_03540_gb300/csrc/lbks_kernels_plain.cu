@@ -140,20 +140,33 @@ __global__ void mass_finalize_kernel(int nruns, const int32_t* __restrict__ tile
   }
 }
 
+// Guard, pass 3: g_0 += (M0 - M)/N at every site of a tile.  The increment is
+// usually far below half an ulp of the stored g_0 (FP32 or FP16), where plain
+// rounding would discard it every time; one thread therefore walks the whole
+// tile and carries the rounding residual (in FP64) to the next site, so the
+// tile as a whole receives its share of the correction to within half an ulp.
+constexpr int kRecentreThreads = 128;
 template <int ST>
-__global__ void __launch_bounds__(kPlainThreads) recentre_kernel(Arena f, const RunDesc* __restrict__ runs,
-                                                                 const Tile* __restrict__ tiles,
-                                                                 const double* __restrict__ delta) {
+__global__ void __launch_bounds__(kRecentreThreads) recentre_kernel(Arena f, const RunDesc* __restrict__ runs,
+                                                                    const Tile* __restrict__ tiles, int ntiles,
+                                                                    const double* __restrict__ delta) {
   using T = typename StorageType<ST>::type;
   using CT = typename StorageType<ST>::compute;
-  const Tile tl = tiles[blockIdx.x];
+  const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ti >= ntiles) return;
+  const Tile tl = tiles[ti];
   const RunDesc& d = runs[tl.run];
   const double dl = delta[tl.run];
   if (dl == 0.0) return;
-  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-    T* p = static_cast<T*>(f.f) + d.off + tl.x0 + k;
-    const double v = static_cast<double>(to_compute(*p, static_cast<CT>(d.scale))) + dl;
-    from_compute(static_cast<CT>(v), static_cast<CT>(d.inv_scale), p);
+  T* base = static_cast<T*>(f.f) + d.off + tl.x0;
+  const CT scale = static_cast<CT>(d.scale), inv = static_cast<CT>(d.inv_scale);
+  double carry = 0.0;
+  for (int k = 0; k < tl.len; ++k) {
+    const double target = static_cast<double>(to_compute(base[k], scale)) + dl + carry;
+    T q;
+    from_compute(static_cast<CT>(target), inv, &q);
+    base[k] = q;
+    carry = target - static_cast<double>(to_compute(q, scale));
   }
 }
 
@@ -228,9 +241,10 @@ cudaError_t launch_mass_finalize(int nruns, const int32_t* tile_begin, const dou
 cudaError_t launch_recentre(int storage, Arena f, const RunDesc* runs, const Tile* tiles, int ntiles,
                             const double* delta, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  if (storage == kF64) recentre_kernel<kF64><<<ntiles, kPlainThreads, 0, s>>>(f, runs, tiles, delta);
-  else if (storage == kF32) recentre_kernel<kF32><<<ntiles, kPlainThreads, 0, s>>>(f, runs, tiles, delta);
-  else if (storage == kF16S) recentre_kernel<kF16S><<<ntiles, kPlainThreads, 0, s>>>(f, runs, tiles, delta);
+  const int blocks = (ntiles + kRecentreThreads - 1) / kRecentreThreads;
+  if (storage == kF64) recentre_kernel<kF64><<<blocks, kRecentreThreads, 0, s>>>(f, runs, tiles, ntiles, delta);
+  else if (storage == kF32) recentre_kernel<kF32><<<blocks, kRecentreThreads, 0, s>>>(f, runs, tiles, ntiles, delta);
+  else if (storage == kF16S) recentre_kernel<kF16S><<<blocks, kRecentreThreads, 0, s>>>(f, runs, tiles, ntiles, delta);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -6,9 +6,11 @@ Tolerances:
    implementation is held to); elsewhere 1e-12 relative to max |rho|.
  * The three kernel families run the same fused arithmetic, so with equal
    storage precision they agree bitwise.
- * FP32: each step rounds Q populations (~Q * 2^-24 relative), a random walk
-   over n steps: the tests bound rel-L2 by 2e-6 * sqrt(n / 1000) * growth,
-   with growth the linear amplification exp(T/4) of KS (T = n dt).
+ * FP32: the collision conserves mass exactly in the rounded arithmetic, so
+   what is left is unbiased rounding: each step rounds Q populations by
+   <= 2^-24 relative, a random walk over n steps.  The tests bound rel-L2 by
+   sqrt(n Q) 2^-24 exp(T/4), exp(T/4) being the largest linear amplification
+   of KS over T = n dt.
 """
 import numpy as np
 import pytest
@@ -124,8 +126,11 @@ def test_fp32_error_against_oracle(lb, kern):
     n, dt = 2000, 1e-4
     ref, _ = ora.run_batch(7, Ns, np.full(4, 0.1), np.full(4, dt), taus, r0, n)
     out, _ = run_gpu(lb, 7, Ns, Ns * 0.1, dt, taus, r0, n, precision=1, kernel=kern, recentre_every=500)
-    rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
-    assert rel <= 2e-6 * np.sqrt(n / 1000) * np.exp(n * dt / 4)
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    bound = np.sqrt(n * 7) * 2.0 ** -24 * np.exp(n * dt / 4)
+    for i in range(Ns.size):
+        a, b = out[off[i]:off[i + 1]], ref[off[i]:off[i + 1]]
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= bound
 
 
 def test_zero_steps_returns_initial_density(lb):
@@ -187,25 +192,36 @@ def test_checkpoint_resume_bitwise(lb, prec):
     np.testing.assert_array_equal(ra, rb)
 
 
+def _mass_after(lb, Ns, r0, prec, every, n):
+    # streaming kernel: the populations are rounded to the storage precision every step
+    h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(Ns.size, 1e-4), np.linspace(1.5, 3.0, Ns.size), r0,
+                            lb.lb_ks_default_opts(precision=prec, recentre_every=every, kernel=2))
+    try:
+        lb.lb_ks_step(h, n)
+        m, e = np.empty(Ns.size), np.empty(Ns.size)
+        lb.lb_ks_mass_energy(h, m, e)
+    finally:
+        lb.lb_ks_free(h)
+    assert np.all(e > 0)
+    return m
+
+
 def test_recentring_holds_the_mass(lb):
     """The FP64 guard returns every run's mass to its initial value (the
-    invariant sum_i f^eq_i = rho) after each recentring."""
+    invariant sum_i f^eq_i = rho) at each guard step, to within the storage
+    granularity: rounding residuals are carried along each 1024-site tile, so at
+    most one half-ulp of g_0 per tile remains."""
     Ns = np.array([1000, 3000, 6000], dtype=np.int64)
     rng = np.random.default_rng(12)
     r0 = np.concatenate([0.5 + 0.01 * rng.standard_normal(n) for n in Ns])
-    m0 = np.array([r0[:1000].sum(), r0[1000:4000].sum(), r0[4000:].sum()])
-    for prec in (1, 2):
-        h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(3, 1e-4), np.array([1.5, 2.0, 3.0]), r0,
-                                lb.lb_ks_default_opts(precision=prec, recentre_every=250))
-        try:
-            lb.lb_ks_step(h, 2000)
-            m, e = np.empty(3), np.empty(3)
-            lb.lb_ks_mass_energy(h, m, e)
-        finally:
-            lb.lb_ks_free(h)
-        tol = 1e-9 if prec == 1 else 1e-4
-        assert np.all(np.abs(m - m0) <= tol * np.abs(m0))
-        assert np.all(e > 0)
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    m0 = np.array([r0[off[i]:off[i + 1]].sum() for i in range(Ns.size)])
+    for prec, ulp in ((1, 2.0 ** -24), (2, 2.0 ** -11)):
+        guarded = np.abs(_mass_after(lb, Ns, r0, prec, 250, 2000) - m0)
+        assert np.all(guarded <= 2 * np.ceil(Ns / 1024) * ulp * 1.0)  # |g_0| < 1 here
+        if prec == 2:  # FP16 storage drifts visibly without the guard
+            free = np.abs(_mass_after(lb, Ns, r0, prec, 0, 2000) - m0)
+            assert np.all(free > 10 * guarded)
 
 
 def test_device_pointers_and_torch_stream(lb):
