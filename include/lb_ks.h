@@ -174,6 +174,13 @@ LB_KS_API int lb_ks_state_bytes(const lb_ks_t *h, size_t *bytes);
  * at least lb_ks_state_bytes bytes).  lb_ks_load restores it into a handle
  * created with the same runs, scheme and precision.  Resuming from a
  * checkpoint gives bitwise the same result as running straight through.
+ * Layout: a 64-byte header; nruns int64 lattice sizes; nruns records of run
+ * constants; nruns FP64 reference masses; last, the populations: scheme
+ * planes of `plane` elements in the storage precision (8, 4 or 2 bytes),
+ * plane = sum over runs of N rounded up to a multiple of 32, run r starting
+ * at the sum of the rounded sizes of the runs before it.  Populations are
+ * stored as f_0 - rhobar, f_1, ..., f_{Q-1} (divided by the run's scale for
+ * F16S), rhobar and scale being the run's initial mean and storage scale.
  */
 LB_KS_API int lb_ks_save(lb_ks_t *h, void *buf, size_t bytes);
 LB_KS_API int lb_ks_load(lb_ks_t *h, const void *buf, size_t bytes);
@@ -200,6 +207,35 @@ LB_KS_API int64_t lb_ks_launches(const lb_ks_t *h);
  * frees a small device buffer.  Errors: LB_KS_EINVAL, LB_KS_ECUDA.
  */
 LB_KS_API int lb_ks_fma_peak(int fp64, double *flops_per_s);
+
+/*
+ * FP64 mass sum_x rho(x) and energy sum_x rho(x)^2 of one lattice whose
+ * populations the caller holds in device memory, computed without allocating
+ * any memory.  No counterpart in the paper: it is the guard's reduction
+ * (lb_ks_mass_energy) for callers that cannot call cudaMalloc -- for instance a
+ * host application whose device memory is all owned by its own pool allocator,
+ * or a monitoring hook that must still work when the device is out of memory.
+ *   f: populations in the library's layout: plane i (i < scheme) starts at
+ *      element i * plane of f, site x at element x of its plane; element type
+ *      double, float or __half for precision LB_KS_F64, LB_KS_F32, LB_KS_F16S
+ *      (the populations section of a checkpoint written by lb_ks_save, run 0,
+ *      has this layout).
+ *   rho(x) = rhobar + scale * sum_i f_i(x)  (rhobar = 0, scale = 1 for FP64;
+ *      for F32 / F16S the run's storage offset and scale).
+ *   out: 2 doubles (mass, energy), host or device memory.
+ * The partial sums live in one static device array of 256 KB (2 x 16384 + 2
+ * doubles), present on every device that loads the library until exit; it
+ * limits N to 2^24 sites (larger N: LB_KS_EINVAL).  The first call on a device
+ * looks the array's address up (cudaGetSymbolAddress) and must be made with
+ * that device current; make that first call before any stream capture on the
+ * device.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Runs on stream (cudaStream_t, NULL = legacy default) and waits for it.
+ * Errors: LB_KS_EINVAL (bad scheme/precision, NULL pointers, N < 1,
+ * N > 2^24, plane < N, scale <= 0), LB_KS_ECUDA.
+ */
+LB_KS_API int lb_ks_mass_energy_noalloc(int scheme, int precision, const void *f, int64_t plane, int64_t N,
+                                        double rhobar, double scale, double *out, void *stream);
 
 /* Release the handle and its device memory.  NULL is ignored. */
 LB_KS_API void lb_ks_free(lb_ks_t *h);

@@ -22,7 +22,8 @@ import numpy as np
 __all__ = [
     "LbKsError", "LbKsOpts", "lb_ks_default_opts", "lb_ks_params", "lb_ks_tau_fit", "lb_ks_init",
     "lb_ks_batch_init", "lb_ks_step", "lb_ks_rho", "lb_ks_mass_energy", "lb_ks_state_bytes", "lb_ks_save",
-    "lb_ks_load", "lb_ks_steps_done", "lb_ks_describe", "lb_ks_launches", "lb_ks_fma_peak", "lb_ks_free",
+    "lb_ks_load", "lb_ks_steps_done", "lb_ks_describe", "lb_ks_launches", "lb_ks_fma_peak",
+    "lb_ks_mass_energy_noalloc", "lb_ks_free",
     "lb_ks_last_error", "library_path", "D1Q5", "D1Q7", "F64", "F32", "F16S", "KERNEL_AUTO", "KERNEL_PLAIN",
     "KERNEL_STREAM", "KERNEL_RESIDENT", "ABI_FUNCTIONS",
 ]
@@ -73,6 +74,8 @@ ABI_FUNCTIONS = {
                                  C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "lb_ks_launches": (C.c_int64, [_P]),
     "lb_ks_fma_peak": (C.c_int, [C.c_int, _PD]),
+    "lb_ks_mass_energy_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int64, C.c_int64, C.c_double, C.c_double, _P,
+                                            _P]),
     "lb_ks_free": (None, [_P]),
     "lb_ks_last_error": (C.c_char_p, [_P]),
 }
@@ -108,7 +111,7 @@ def _ptr(a, dtype=np.float64):
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        if (dtype is not None and a.dtype != dtype) or not a.flags["C_CONTIGUOUS"]:
             raise ValueError(f"expected a contiguous {np.dtype(dtype).name} array")
         return a.ctypes.data
     if hasattr(a, "data_ptr"):
@@ -213,6 +216,15 @@ def lb_ks_fma_peak(fp64: bool) -> float:
     rc = _load().lb_ks_fma_peak(int(bool(fp64)), C.byref(v))
     _check(rc)
     return v.value
+
+
+def lb_ks_mass_energy_noalloc(scheme: int, precision: int, f, plane: int, N: int, rhobar: float, scale: float,
+                              out, stream=None) -> None:
+    """Mass and energy of populations held by the caller (device memory), with no allocation."""
+    s = getattr(stream, "cuda_stream", stream)
+    rc = _load().lb_ks_mass_energy_noalloc(scheme, precision, _ptr(f, None), int(plane), int(N), float(rhobar),
+                                           float(scale), _ptr(out), C.c_void_p(int(s) if s else 0))
+    _check(rc)
 
 
 def lb_ks_free(h) -> None:
