@@ -39,6 +39,15 @@ int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 size_t storage_bytes(int prec) { return prec == kF64 ? 8 : (prec == kF32 ? 4 : 2); }
 
+// One resident-kernel work list: bundles of pieces, launched k steps at a time on `grid` blocks.
+struct Lane {
+  bool segmented = false;
+  int k = 0, grid = 0, nbundles = 0;
+  Piece* d_pieces = nullptr;
+  int2* d_bundles = nullptr;
+  int* d_queue = nullptr;
+};
+
 }  // namespace
 
 struct lb_ks {
@@ -65,14 +74,14 @@ struct lb_ks {
   double* d_energy = nullptr;
   double* d_delta = nullptr;
   int* d_flags = nullptr;
-  // resident kernel
-  int S = 0, NT = 0, kmax = 0, grid = 0, nbundles = 0;
-  Piece* d_pieces = nullptr;
-  int2* d_bundles = nullptr;
-  int* d_queue = nullptr;
+  // resident kernel: lanes[0] rings (or segments if there are no rings), lanes[1] segments
+  int S = 0, NT = 0, kmax = 0, kseg = 0, nlanes = 0;
+  Lane lanes[2];
   // scheduling
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;  // second lane of the resident kernel
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t steps_done = 0;
   int64_t phase = 0;  // steps since the last guard
   int64_t launches = 0;
@@ -134,9 +143,12 @@ bool valid_opts(const lb_ks_opts& o, std::string* why) {
 
 // ---------------------------------------------------------------- planning
 
-// Ring or segment pieces of every run for (S, NT, k); false if some run cannot be held.
-bool plan_pieces(const lb_ks* h, int S, int NT, int k, std::vector<Piece>* out) {
-  out->clear();
+// Pieces of every run for (S, NT): rings (whole lattices) and segments (for lattices
+// longer than one block holds, with c_max * kseg halo sites per side); false if
+// some run cannot be held.
+bool plan_pieces(const lb_ks* h, int S, int NT, int kseg, std::vector<Piece>* rings, std::vector<Piece>* segs) {
+  rings->clear();
+  segs->clear();
   const int C = h->cmax;
   for (int32_t r = 0; r < h->nruns; ++r) {
     const int64_t N = h->N[r];
@@ -152,13 +164,13 @@ bool plan_pieces(const lb_ks* h, int S, int NT, int k, std::vector<Piece>* out) 
       if (n > V * (S - 1)) {
         Piece p{};
         p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n; p.x0 = 0; p.st_lo = 0; p.st_hi = (int)N;
-        out->push_back(p);
+        rings->push_back(p);
         ring = true;
         break;
       }
     }
     if (ring) continue;
-    const int64_t h2 = 2LL * C * k;
+    const int64_t h2 = 2LL * C * kseg;
     const int64_t room = (int64_t)NT * S - h2 - 2 * S;
     if (room <= 0) return false;
     const int64_t nseg = (N + room - 1) / room;
@@ -171,9 +183,9 @@ bool plan_pieces(const lb_ks* h, int S, int NT, int k, std::vector<Piece>* out) 
       if (V > NT) return false;
       Piece p{};
       p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n;
-      p.x0 = ((s0 - (int64_t)C * k) % N + N) % N;
-      p.st_lo = C * k; p.st_hi = (int)(C * k + len);
-      out->push_back(p);
+      p.x0 = ((s0 - (int64_t)C * kseg) % N + N) % N;
+      p.st_lo = C * kseg; p.st_hi = (int)(C * kseg + len);
+      segs->push_back(p);
     }
   }
   return true;
@@ -212,6 +224,25 @@ int default_threads(int prec, int S) {
   return S <= 8 ? 512 : (S <= 12 ? 384 : 256);
 }
 
+int upload_lane(lb_ks* h, Lane* L, std::vector<Piece>& pieces, int NT, int k) {
+  std::vector<Piece> ordered;
+  std::vector<int2> bundles;
+  pack_bundles(pieces, NT, &ordered, &bundles);
+  int rc;
+  if ((rc = dalloc(h, &L->d_pieces, ordered.size()))) return rc;
+  if ((rc = dalloc(h, &L->d_bundles, bundles.size()))) return rc;
+  if ((rc = dalloc(h, &L->d_queue, 1))) return rc;
+  LBKS_CUDA(h, cudaMemcpy(L->d_pieces, ordered.data(), ordered.size() * sizeof(Piece), cudaMemcpyHostToDevice), "upload pieces");
+  LBKS_CUDA(h, cudaMemcpy(L->d_bundles, bundles.data(), bundles.size() * sizeof(int2), cudaMemcpyHostToDevice), "upload bundles");
+  L->k = k;
+  L->nbundles = (int)bundles.size();
+  return LB_KS_OK;
+}
+
+// Resident kernel plan.  Whole lattices (rings) run k_ring steps per launch; lattices
+// cut into segments run k_seg-step launches (their halo grows with the steps per
+// launch).  When both kinds exist they run as two lanes on disjoint sets of blocks,
+// on two streams, sized so that both finish a chunk of steps at about the same time.
 int setup_resident(lb_ks* h, bool required) {
   std::vector<int> cand;
   if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
@@ -221,42 +252,74 @@ int setup_resident(lb_ks* h, bool required) {
   for (int S : cand) {
     const int NT = h->opts.threads_per_block ? h->opts.threads_per_block : default_threads(h->prec, S);
     if (!resident_supported(h->Q, h->prec, S, NT)) continue;
-    int k = h->opts.steps_per_launch;
-    std::vector<Piece> pieces;
-    if (k == 0) {
-      k = R > 0 ? std::min(R, 1000) : 1000;
-      // with segments, keep the halo work near 10% of a block's sites
-      if (!plan_pieces(h, S, NT, k, &pieces) || pieces.size() != (size_t)h->nruns) {
-        const int kseg = std::max(1, (int)((int64_t)NT * S / (20 * h->cmax)));
-        k = std::min(k, kseg);
-        if (R > 0) while (R % k) --k;  // launches end on guard steps
-      }
-    }
-    if (!plan_pieces(h, S, NT, k, &pieces)) continue;
-    std::vector<Piece> ordered;
-    std::vector<int2> bundles;
-    pack_bundles(pieces, NT, &ordered, &bundles);
+    const int kring = h->opts.steps_per_launch ? h->opts.steps_per_launch : (R > 0 ? std::min(R, 1000) : 1000);
+    int kseg = h->opts.steps_per_launch ? h->opts.steps_per_launch
+                                        : std::max(1, (int)((int64_t)NT * S / (20 * h->cmax)));
+    kseg = std::min(kseg, kring);
+    std::vector<Piece> rings, segs;
+    if (!plan_pieces(h, S, NT, kseg, &rings, &segs)) continue;
     int bps = 0;
     cudaError_t e = resident_prepare(h->Q, h->prec, S, NT, &bps);
     if (e != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
     int dev = 0, sms = 0;
     LBKS_CUDA(h, cudaGetDevice(&dev), "cudaGetDevice");
     LBKS_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    const int slots = bps * sms;
     int rc;
-    if ((rc = dalloc(h, &h->d_pieces, ordered.size()))) return rc;
-    if ((rc = dalloc(h, &h->d_bundles, bundles.size()))) return rc;
-    if ((rc = dalloc(h, &h->d_queue, 1))) return rc;
-    LBKS_CUDA(h, cudaMemcpy(h->d_pieces, ordered.data(), ordered.size() * sizeof(Piece), cudaMemcpyHostToDevice), "upload pieces");
-    LBKS_CUDA(h, cudaMemcpy(h->d_bundles, bundles.data(), bundles.size() * sizeof(int2), cudaMemcpyHostToDevice), "upload bundles");
+    h->nlanes = 0;
+    if (!rings.empty()) {
+      if ((rc = upload_lane(h, &h->lanes[h->nlanes], rings, NT, kring))) return rc;
+      h->lanes[h->nlanes++].segmented = false;
+    }
+    if (!segs.empty()) {
+      if ((rc = upload_lane(h, &h->lanes[h->nlanes], segs, NT, kseg))) return rc;
+      h->lanes[h->nlanes++].segmented = true;
+    }
+    if (h->nlanes == 1) {
+      h->lanes[0].grid = std::min(h->lanes[0].nbundles, slots);
+    } else {
+      // Split the blocks: ring bundles take ceil(B1/G1) rounds of k_ring steps, segment
+      // bundles ceil(B2/G2) rounds of the same steps plus their launch-edge and halo
+      // overhead (weighted 1.25).
+      const int B1 = h->lanes[0].nbundles, B2 = h->lanes[1].nbundles;
+      int best = 1;
+      double bestT = 1e300;
+      for (int G1 = 1; G1 < slots; ++G1) {
+        const int G2 = slots - G1;
+        const double T = std::max<double>((B1 + G1 - 1) / G1, 1.25 * ((B2 + G2 - 1) / G2));
+        if (T < bestT) { bestT = T; best = G1; }
+      }
+      h->lanes[0].grid = std::min(B1, best);
+      h->lanes[1].grid = std::min(B2, slots - best);
+    }
     h->S = S;
     h->NT = NT;
-    h->kmax = k;
-    h->nbundles = (int)bundles.size();
-    h->grid = std::min(h->nbundles, bps * sms);
+    h->kmax = h->lanes[0].segmented ? kseg : kring;
+    h->kseg = kseg;
     return LB_KS_OK;
   }
   if (required) return fail(h, LB_KS_EINVAL, "resident kernel cannot hold these lattices with the requested tiling");
   return 1;  // not possible; caller picks another family
+}
+
+// k steps of one lane starting from arena `from`, in launches of at most lane.k steps,
+// alternating arenas.  Returns the arena holding the result; a single launch may write
+// in place (to == from) when `in_place` is set.
+int issue_lane(lb_ks* h, const Lane& L, int64_t k, int from, bool in_place, cudaStream_t s, int64_t* nk, int* to) {
+  int cur = from;
+  while (k > 0) {
+    const int64_t kk = std::min<int64_t>(k, L.k);
+    const int dst = (in_place && kk == k && cur == from) ? cur : 1 - cur;
+    LBKS_CUDA(h, cudaMemsetAsync(L.d_queue, 0, sizeof(int), s), "queue reset");
+    ResidentLaunch RL{h->Q, h->prec, h->S, h->NT, arena(h, cur), arena(h, dst), h->d_runs,
+                      L.d_pieces, L.d_bundles, L.nbundles, L.d_queue, (int)kk, L.grid};
+    LBKS_CUDA(h, launch_resident(RL, s), "resident step");
+    *nk += 1;
+    cur = dst;
+    k -= kk;
+  }
+  *to = cur;
+  return LB_KS_OK;
 }
 
 // ---------------------------------------------------------------- step scheduling
@@ -283,19 +346,35 @@ int issue_steps(lb_ks* h, int64_t n, cudaStream_t s, int64_t* nk) {
     if (h->kernel == LB_KS_KERNEL_RESIDENT) {
       k = std::min<int64_t>(n, h->kmax);
       if (R > 0) k = std::min<int64_t>(k, R - h->phase);
-      LBKS_CUDA(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), s), "queue reset");
-      ResidentLaunch L{h->Q, h->prec, h->S, h->NT, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
-                       h->d_pieces, h->d_bundles, h->nbundles, h->d_queue, (int)k, h->grid};
-      LBKS_CUDA(h, launch_resident(L, s), "resident step");
-    } else if (h->kernel == LB_KS_KERNEL_STREAM) {
-      LBKS_CUDA(h, launch_stream_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
-                                      h->d_stream_tiles, h->n_stream_tiles, s), "stream step");
+      int to = h->cur, rc;
+      if (h->nlanes == 1) {
+        if ((rc = issue_lane(h, h->lanes[0], k, h->cur, false, s, nk, &to))) return rc;
+      } else {
+        // segments on the side stream; rings on s, one launch, ending in the same arena
+        const int64_t mseg = (k + h->lanes[1].k - 1) / h->lanes[1].k;
+        LBKS_CUDA(h, cudaEventRecord(h->ev_fork, s), "fork");
+        LBKS_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0), "fork wait");
+        int to_seg = h->cur;
+        if ((rc = issue_lane(h, h->lanes[1], k, h->cur, false, h->side_stream, nk, &to_seg))) return rc;
+        Lane ring = h->lanes[0];
+        ring.k = (int)k;
+        if ((rc = issue_lane(h, ring, k, h->cur, (mseg % 2) == 0, s, nk, &to))) return rc;
+        LBKS_CUDA(h, cudaEventRecord(h->ev_join, h->side_stream), "join");
+        LBKS_CUDA(h, cudaStreamWaitEvent(s, h->ev_join, 0), "join wait");
+        if (to != to_seg) return fail(h, LB_KS_ECUDA, "internal: lanes ended in different arenas");
+      }
+      h->cur = to;
     } else {
-      LBKS_CUDA(h, launch_plain_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
-                                     h->d_plain_tiles, h->n_plain_tiles, s), "plain step");
+      if (h->kernel == LB_KS_KERNEL_STREAM) {
+        LBKS_CUDA(h, launch_stream_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
+                                        h->d_stream_tiles, h->n_stream_tiles, s), "stream step");
+      } else {
+        LBKS_CUDA(h, launch_plain_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
+                                       h->d_plain_tiles, h->n_plain_tiles, s), "plain step");
+      }
+      *nk += 1;
+      h->cur = 1 - h->cur;
     }
-    *nk += 1;
-    h->cur = 1 - h->cur;
     n -= k;
     h->steps_done += k;
     if (R > 0) {
@@ -518,6 +597,12 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     return bail(cuda_fail(h, ce, "stream kernel setup"));
   if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "create capture stream"));
+  if (h->nlanes == 2) {
+    if ((ce = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+      return bail(cuda_fail(h, ce, "create lane stream"));
+  }
 
   // f = f^eq(rho0).
   if ((ce = launch_init_eq(scheme, h->prec, arena(h, 0), h->d_runs, h->d_stream_tiles, h->n_stream_tiles, h->d_stage,
@@ -694,8 +779,12 @@ void lb_ks_free(lb_ks_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  if (h->side_stream) cudaStreamSynchronize(h->side_stream);
   for (void* p : h->allocations) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   cudaGetLastError();
   delete h;
 }

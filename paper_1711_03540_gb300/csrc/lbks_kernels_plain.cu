@@ -76,24 +76,73 @@ __global__ void __launch_bounds__(kPlainThreads) plain_step_kernel(Arena src, Ar
     from_compute(g[i], k.inv_scale, fd + (int64_t)i * dst.plane + wrap_site(x + speed(i), d.N));
 }
 
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum, six rounded operations).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// FP64 rho and rho^2 sums of the sites k0, k0 + stride, ... < len of one tile.
+// FP64 storage: plain FP64 arithmetic.  FP32/FP16 storage: the per-site sum and the
+// per-thread accumulators are kept as unevaluated pairs of floats (TwoSum), which
+// carries ~48 bits through GB300's wide FP32 pipe instead of its narrow FP64 pipe;
+// the pairs are converted to FP64 once per thread.
+template <int Q, int ST>
+__device__ __forceinline__ void site_sums(const typename StorageType<ST>::type* f, int64_t plane, const RunDesc& d,
+                                          int k0, int len, int stride, double& m, double& e) {
+  using CT = typename StorageType<ST>::compute;
+  if constexpr (ST == kF64) {
+    m = 0.0;
+    e = 0.0;
+    for (int k = k0; k < len; k += stride) {
+      double rho = d.rhobar;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) rho += f[(int64_t)i * plane + k];
+      m += rho;
+      e = __fma_rn(rho, rho, e);
+    }
+  } else {
+    const float rb_hi = (float)d.rhobar, rb_lo = (float)(d.rhobar - (double)rb_hi);
+    float mh = 0.f, ml = 0.f, eh = 0.f, el = 0.f;
+    for (int k = k0; k < len; k += stride) {
+      float hi = rb_hi, lo = rb_lo, t, te;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        two_sum(hi, to_compute(f[(int64_t)i * plane + k], static_cast<CT>(d.scale)), t, te);
+        hi = t;
+        lo = __fadd_rn(lo, te);
+      }
+      two_sum(hi, lo, hi, lo);  // renormalise
+      two_sum(mh, hi, t, te);
+      mh = t;
+      ml = __fadd_rn(ml, __fadd_rn(te, lo));
+      const float p = __fmul_rn(hi, hi);
+      const float pe = __fmaf_rn(hi, hi, -p);  // exact low part of hi^2
+      two_sum(eh, p, t, te);
+      eh = t;
+      el = __fadd_rn(el, __fadd_rn(te, __fmaf_rn(2.f * hi, lo, pe)));
+    }
+    m = (double)mh + (double)ml;
+    e = (double)eh + (double)el;
+  }
+}
+
 // Guard, pass 1: FP64 sums of rho and rho^2 over one tile (fixed-order tree).
 template <int Q, int ST>
 __global__ void __launch_bounds__(kPlainThreads) mass_partials_kernel(Arena src, const RunDesc* __restrict__ runs,
                                                                       const Tile* __restrict__ tiles,
                                                                       double* __restrict__ partials) {
   using T = typename StorageType<ST>::type;
-  using CT = typename StorageType<ST>::compute;
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
-  double m = 0.0, e = 0.0;
-  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-    const T* f = static_cast<const T*>(src.f) + d.off + tl.x0 + k;
-    double rho = d.rhobar;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) rho += static_cast<double>(to_compute(f[(int64_t)i * src.plane], static_cast<CT>(d.scale)));
-    m += rho;
-    e = __fma_rn(rho, rho, e);
-  }
+  double m, e;
+  site_sums<Q, ST>(static_cast<const T*>(src.f) + d.off + tl.x0, src.plane, d, threadIdx.x, tl.len, blockDim.x, m, e);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     m += __shfl_xor_sync(0xffffffffu, m, o);
@@ -142,32 +191,48 @@ __global__ void mass_finalize_kernel(int nruns, const int32_t* __restrict__ tile
 
 // Guard, pass 3: g_0 += (M0 - M)/N at every site of a tile.  The increment is
 // usually far below half an ulp of the stored g_0 (FP32 or FP16), where plain
-// rounding would discard it every time; one thread therefore walks the whole
-// tile and carries the rounding residual (in FP64) to the next site, so the
-// tile as a whole receives its share of the correction to within half an ulp.
-constexpr int kRecentreThreads = 128;
+// rounding would discard it every time.  One warp per tile: each lane walks a
+// contiguous chunk and carries the exact rounding residual (TwoSum) to its next
+// site; the lanes' leftover residuals are then summed and added to the tile's
+// first site, so the tile as a whole receives its share of the correction to
+// within half an ulp.  Arithmetic in the compute type (FP32 for FP32/FP16).
+constexpr int kRecentreThreads = 32;
+template <int ST>
+__device__ __forceinline__ typename StorageType<ST>::compute add_carry(typename StorageType<ST>::type* p,
+                                                                        typename StorageType<ST>::compute inc,
+                                                                        typename StorageType<ST>::compute scale,
+                                                                        typename StorageType<ST>::compute inv) {
+  using CT = typename StorageType<ST>::compute;
+  using T = typename StorageType<ST>::type;
+  const CT v = to_compute(*p, scale);
+  CT t, te;
+  two_sum(v, inc, t, te);  // t + te == v + inc exactly
+  T q;
+  from_compute(t, inv, &q);
+  *p = q;
+  return add_rn(add_rn(t, -to_compute(q, scale)), te);  // (v + inc) - stored value
+}
+
 template <int ST>
 __global__ void __launch_bounds__(kRecentreThreads) recentre_kernel(Arena f, const RunDesc* __restrict__ runs,
-                                                                    const Tile* __restrict__ tiles, int ntiles,
+                                                                    const Tile* __restrict__ tiles,
                                                                     const double* __restrict__ delta) {
   using T = typename StorageType<ST>::type;
   using CT = typename StorageType<ST>::compute;
-  const int ti = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ti >= ntiles) return;
-  const Tile tl = tiles[ti];
+  const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
-  const double dl = delta[tl.run];
-  if (dl == 0.0) return;
+  const CT dl = static_cast<CT>(delta[tl.run]);
+  if (dl == CT(0)) return;
   T* base = static_cast<T*>(f.f) + d.off + tl.x0;
   const CT scale = static_cast<CT>(d.scale), inv = static_cast<CT>(d.inv_scale);
-  double carry = 0.0;
-  for (int k = 0; k < tl.len; ++k) {
-    const double target = static_cast<double>(to_compute(base[k], scale)) + dl + carry;
-    T q;
-    from_compute(static_cast<CT>(target), inv, &q);
-    base[k] = q;
-    carry = target - static_cast<double>(to_compute(q, scale));
-  }
+  const int chunk = (tl.len + 31) / 32;
+  const int k0 = threadIdx.x * chunk, k1 = min(tl.len, k0 + chunk);
+  CT carry = CT(0);
+  for (int k = k0; k < k1; ++k) carry = add_carry<ST>(base + k, add_rn(dl, carry), scale, inv);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) carry = add_rn(carry, __shfl_xor_sync(0xffffffffu, carry, o));
+  __syncwarp();
+  if (threadIdx.x == 0) add_carry<ST>(base, carry, scale, inv);
 }
 
 // FMA-pipe micro-benchmark: independent chains of fused multiply-adds.
@@ -241,10 +306,9 @@ cudaError_t launch_mass_finalize(int nruns, const int32_t* tile_begin, const dou
 cudaError_t launch_recentre(int storage, Arena f, const RunDesc* runs, const Tile* tiles, int ntiles,
                             const double* delta, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  const int blocks = (ntiles + kRecentreThreads - 1) / kRecentreThreads;
-  if (storage == kF64) recentre_kernel<kF64><<<blocks, kRecentreThreads, 0, s>>>(f, runs, tiles, ntiles, delta);
-  else if (storage == kF32) recentre_kernel<kF32><<<blocks, kRecentreThreads, 0, s>>>(f, runs, tiles, ntiles, delta);
-  else if (storage == kF16S) recentre_kernel<kF16S><<<blocks, kRecentreThreads, 0, s>>>(f, runs, tiles, ntiles, delta);
+  if (storage == kF64) recentre_kernel<kF64><<<ntiles, kRecentreThreads, 0, s>>>(f, runs, tiles, delta);
+  else if (storage == kF32) recentre_kernel<kF32><<<ntiles, kRecentreThreads, 0, s>>>(f, runs, tiles, delta);
+  else if (storage == kF16S) recentre_kernel<kF16S><<<ntiles, kRecentreThreads, 0, s>>>(f, runs, tiles, delta);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

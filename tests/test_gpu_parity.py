@@ -105,6 +105,22 @@ def test_kernel_families_agree_bitwise(lb, prec):
     np.testing.assert_array_equal(outs[0], seg)
 
 
+@pytest.mark.parametrize("n", [240, 228])
+def test_two_lane_resident_schedule_bitwise(lb, n):
+    """Whole lattices and segmented ones run as two concurrent lanes (rings: one
+    launch per chunk, in place when the segment lane makes an even number of
+    launches; segments: many short launches).  Both parities of the segment
+    launch count give the plain kernel's result bitwise."""
+    Ns = np.array([300, 700, 3000, 5000], dtype=np.int64)
+    rng = np.random.default_rng(31)
+    r0 = np.concatenate([0.01 * rng.standard_normal(k) for k in Ns])
+    args = (7, Ns, Ns * 0.1, np.full(4, 1e-4), np.array([1.5, 2.0, 2.5, 3.0]), r0, n)
+    ref = run_gpu(lb, *args, precision=1, kernel=1)[0]
+    out, desc = run_gpu(lb, *args, precision=1, kernel=3, threads_per_block=64)
+    assert desc["kernel"] == 3
+    np.testing.assert_array_equal(ref, out)
+
+
 def test_f16s_resident_one_step_per_launch_equals_stream(lb):
     Ns = np.array([640, 2000], dtype=np.int64)
     rng = np.random.default_rng(4)
