@@ -43,6 +43,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--nruns", type=int, default=4096)
+    p.add_argument("--nmax", type=int, default=8192, help="largest lattice of the ensemble (profiling variants)")
+    p.add_argument("--workload", default="ensemble", choices=["ensemble", "long"],
+                   help="ensemble: 4096 lattices (default); long: one lattice of 2^24 sites")
+    p.add_argument("--kernel", default="resident", choices=["resident", "stream", "plain"])
+    p.add_argument("--precision", default="f32", choices=["f32", "f16s", "f64"])
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
     return p.parse_args()
 
@@ -174,9 +179,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lbbuild.build()
     stream = torch.cuda.Stream()
-    wl = workloads.ensemble(nruns=args.nruns, seed=workloads.BASE_SEED + rank * args.nruns)
+    if args.workload == "long":
+        wl = workloads.long_lattice(seed=workloads.BASE_SEED + rank)
+    else:
+        wl = workloads.ensemble(nruns=args.nruns, nmax=args.nmax, seed=workloads.BASE_SEED + rank * args.nruns)
     Q = wl.scheme
-    opts = lb.lb_ks_default_opts(precision=lb.F32, recentre_every=GUARD_EVERY, kernel=lb.KERNEL_RESIDENT,
+    prec = {"f32": lb.F32, "f16s": lb.F16S, "f64": lb.F64}[args.precision]
+    kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN}[args.kernel]
+    opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
                                  stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
     desc = lb.lb_ks_describe(h)
@@ -212,30 +222,55 @@ def main():
     updates = sites * LB_STEPS_PER_STEP * args.steps
     value = updates * ws / (total_ms * 1e-3)
 
-    # Roofline of the dominant kernel (the resident kernel): FP32 ALU.
+    # Roofline of the dominant kernel.
     k = desc["steps_per_launch"]
-    res_launches_per_step = -(-LB_STEPS_PER_STEP // k)
-    launch_ms = statistics.mean(step_ms) / res_launches_per_step  # guard kernels (<1%) are charged to it
-    flops_per_launch = FLOP_PER_SITE_UPDATE[Q] * sites * k
+    step_mean_ms = statistics.mean(step_ms)
     smax = clocks.get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(local)
-    peak_tflops = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12
-    achieved = flops_per_launch / (launch_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "traffic": None, "kernel": "resident_kernel<7,F32,%d>" % desc["sites_per_thread"],
-                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (derived)",
-                "algorithmic": f"{FLOP_PER_SITE_UPDATE[Q]} flop/site-update x {sites} sites x {k} steps per launch"}
+    elem = {lb.F64: 8, lb.F32: 4, lb.F16S: 2}[prec]
+    kname = {lb.KERNEL_RESIDENT: "resident_kernel", lb.KERNEL_STREAM: "stream_step_kernel",
+             lb.KERNEL_PLAIN: "plain_step_kernel"}[desc["kernel"]]
+    kname += "<%d,%s%s>" % (Q, args.precision.upper(), ",%d" % desc["sites_per_thread"] if desc["sites_per_thread"] else "")
+    if desc["kernel"] == lb.KERNEL_RESIDENT or prec == lb.F64:
+        # Arithmetic-bound.  The resident kernel's two lanes (whole lattices: one launch per
+        # 500 steps; segmented lattices: short launches on a second stream) overlap, so the
+        # launches of one benchmark step are timed together: algorithmic flops of the step /
+        # CUDA-event step time (the guard's few-percent share is charged to the kernel).
+        flops_per_step = FLOP_PER_SITE_UPDATE[Q] * sites * LB_STEPS_PER_STEP
+        achieved = flops_per_step / (step_mean_ms * 1e-3) / 1e12
+        if prec == lb.F64:
+            peak, basis = 1.25, "nominal GB300 FP64 rate (1.25 TFLOP/s)"
+        else:
+            peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12
+            basis = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (derived)"
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": kname, "peak_basis": basis,
+                    "algorithmic": f"{FLOP_PER_SITE_UPDATE[Q]} flop/site-update x {sites} sites x "
+                                   f"{LB_STEPS_PER_STEP} steps per benchmark step",
+                    "time_basis": "CUDA events around each benchmark step on the launching stream"}
+    else:
+        # HBM-bound, one launch per LB step: per launch one read and one write of the Q planes.
+        peaks, src = measured_peaks()
+        bytes_per_launch = 2 * Q * elem * sites
+        launch_s = step_mean_ms * 1e-3 / LB_STEPS_PER_STEP
+        achieved = bytes_per_launch / launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname,
+                    "peak_basis": f"hbm_gbs of MEASURED_PEAKS.json ({src})",
+                    "algorithmic": f"{2 * Q * elem} B/site-update x {sites} sites per launch",
+                    "time_basis": "CUDA-event benchmark-step time / launches per step (guard charged to the kernel)"}
     line = {"metric": "lattice-site updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": wl.name, "scheme": "D1Q7", "nruns": wl.nruns, "sites": sites,
-                       "lb_steps_per_step": LB_STEPS_PER_STEP, "storage": "f32 deviations", "guard_every": GUARD_EVERY,
-                       "kernel": "resident", "sites_per_thread": desc["sites_per_thread"],
-                       "threads_per_block": desc["threads_per_block"], "steps_per_launch": k,
-                       "l2": f"state {sites * Q * 4 / 1e6:.0f} MB > 129 MB L2 (no flush needed)"},
+                       "lb_steps_per_step": LB_STEPS_PER_STEP, "storage": args.precision + " (f_0 stored as deviation)",
+                       "guard_every": 0 if prec == lb.F64 else GUARD_EVERY, "kernel": args.kernel,
+                       "sites_per_thread": desc["sites_per_thread"], "threads_per_block": desc["threads_per_block"],
+                       "steps_per_launch": k,
+                       "l2": f"state {sites * Q * elem / 1e6:.0f} MB > 129 MB L2 (no flush needed)"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches)}
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and args.workload == "ensemble" and args.kernel == "resident":
         extras(lb, torch, wl, h, stream, line, local)
     lb.lb_ks_free(h)
     if rank == 0:

@@ -67,8 +67,14 @@ __device__ __forceinline__ void from_compute(float v, float inv_scale, __half* p
 // by (1 + O(ulp)) per step (in FP32 a 1e-5 relative error after ~2000 steps).
 // rho a_i is shared by the pair +-c; rho^2 b_i enters through an fma, so the small
 // advection term is rounded relative to rho a_i (whose low bits change every step).
-// Summation order and fma forms are fixed here: every kernel family produces bitwise
-// the same post-collision values from the same inputs.
+// Summation order and fma forms are fixed here (g_0 = sum_i g_i minus g*_{+1}, g*_{-1},
+// g*_{+2}, ... in that order): every kernel family, including the resident kernel's
+// plane-by-plane form of the same arithmetic, produces bitwise the same values.
+template <typename CT>
+__device__ __forceinline__ CT post_collision(CT r, CT g, CT rho, CT rho2, CT b, CT t) {
+  return fma_rn(r, g, fma_rn(rho2, b, t));
+}
+
 template <int Q, typename CT>
 __device__ __forceinline__ void collide(CT (&g)[Q], const Coef<CT, Q>& k) {
   CT sg = g[0];
@@ -76,16 +82,16 @@ __device__ __forceinline__ void collide(CT (&g)[Q], const Coef<CT, Q>& k) {
   for (int i = 1; i < Q; ++i) sg = add_rn(sg, g[i]);
   const CT rho = add_rn(k.rhobar, sg);
   const CT rho2 = mul_rn(rho, rho);
-  CT acc = CT(0);
+  CT acc = sg;
 #pragma unroll
   for (int p = 1; 2 * p < Q; ++p) {  // speeds +p (index 2p-1) and -p (index 2p)
     const CT t = mul_rn(rho, k.a[2 * p - 1]);  // a_{+p} = a_{-p}
-    g[2 * p - 1] = fma_rn(k.r, g[2 * p - 1], fma_rn(rho2, k.b[2 * p - 1], t));
-    g[2 * p] = fma_rn(k.r, g[2 * p], fma_rn(rho2, k.b[2 * p], t));
-    const CT s = add_rn(g[2 * p - 1], g[2 * p]);
-    acc = p == 1 ? s : add_rn(acc, s);
+    g[2 * p - 1] = post_collision(k.r, g[2 * p - 1], rho, rho2, k.b[2 * p - 1], t);
+    acc = add_rn(acc, -g[2 * p - 1]);
+    g[2 * p] = post_collision(k.r, g[2 * p], rho, rho2, k.b[2 * p], t);
+    acc = add_rn(acc, -g[2 * p]);
   }
-  g[0] = add_rn(sg, -acc);
+  g[0] = acc;
 }
 
 __device__ __forceinline__ int64_t wrap_site(int64_t x, int64_t N) {

@@ -86,7 +86,6 @@ struct ResidentLaunch {
 };
 bool resident_supported(int Q, int storage, int S, int NT);
 cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm);
-size_t resident_smem_bytes(int Q, int storage, int NT);
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
 
 // Diagnostic micro-benchmark of the FMA pipes (flop/s), used by the benchmark

@@ -1,5 +1,5 @@
 // Register-resident, temporally blocked fused step for ensembles of lattices
-// (one persistent launch runs ksteps steps of every lattice of the batch).
+// (one persistent launch runs ksteps steps of every lattice it is given).
 //
 // Work unit ("piece"): a whole periodic lattice (ring) or, for lattices larger
 // than one block holds, a stretch of one with c_max * ksteps halo sites on
@@ -9,17 +9,25 @@
 // different runs (different N, tau, alpha, beta) are packed into the same
 // block by the host ("bundle").
 //
-// One step = collide every held site in registers (Eq. LB_equation_ordinary),
-// then shift plane i by c_i: inside a thread by register renaming, across
-// threads by writing the c_i values that leave a thread into shared memory,
-// one barrier, and reading the ones that enter from the neighbour thread
-// (the neighbour of the piece's last thread is its first: periodic wrap).
-// For a segment the wrap injects unrelated values at its two ends; they
-// travel at most c_max sites per step and never reach the stored middle.
+// One step of Eq. LB_equation_ordinary:
+//  A. per held site: s_g = sum_i g_i, rho = rhobar + s_g, rho^2;
+//  B. per plane i >= 1, the post-collision value of every site is written
+//     straight into the register of the site it streams to (c_i > 0: sites
+//     visited from the last one down, c_i < 0: from the first one up, so the
+//     destination register's old value has already been used); the c_i values
+//     that leave the thread go to shared memory;  g_0 = s_g - sum of the others
+//     (mass conservation; the same arithmetic, in the same order, as collide());
+//  C. one barrier, then the values entering from the neighbour thread are read
+//     (the neighbour of a piece's last thread is its first: periodic wrap).
+// For a segment the wrap injects unrelated values at its two ends; they travel
+// at most c_max sites per step and never reach the stored middle.
+//
+// Loads and stores at the launch edges go through shared memory so that
+// global accesses are coalesced (consecutive threads, consecutive sites).
 //
 // Blocks take bundles from a global counter (atomicAdd), largest first, until
-// the queue is empty: a persistent grid with a ragged work queue.  There are no
-// waits on other blocks.
+// the queue is empty: a persistent grid with a ragged work queue.  No block
+// waits on another.
 #include <type_traits>
 
 #include "lbks_device.cuh"
@@ -53,6 +61,14 @@ struct ResidentArgs {
   int ksteps;
 };
 
+// Shared memory per thread (elements): the exchange buffers
+// [2 parities][2 directions][NX], reused at the launch edges as a staging area
+// of Q planes x S sites.
+__host__ __device__ constexpr int exchange_elems(int Q) { return 4 * ((Q - 1) / 2) * ((Q - 1) / 2 + 1) / 2; }
+__host__ __device__ constexpr int smem_elems_per_thread(int Q, int S) {
+  return exchange_elems(Q) > Q * S ? exchange_elems(Q) : Q * S;
+}
+
 template <int Q, int ST, int S>
 __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_kernel(const ResidentArgs a) {
   using T = typename StorageType<ST>::type;
@@ -61,8 +77,8 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
   constexpr int NX = C * (C + 1) / 2;  // values leaving a thread per direction per step
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NT = blockDim.x;
-  CT* xR = reinterpret_cast<CT*>(smem_raw);  // [2 parities][NX][NT]: right-moving values
-  CT* xL = xR + 2 * NX * NT;                  // [2 parities][NX][NT]: left-moving values
+  CT* const xbase = reinterpret_cast<CT*>(smem_raw);  // [parity][R|L][NX][NT]
+  CT* const stage = xbase;                             // [NT * S] at the launch edges
   __shared__ int s_bundle;
   const int t = threadIdx.x;
 
@@ -84,118 +100,153 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
     CT f[Q][S];
     Coef<CT, Q> k;
     bool full = true;
-    int start = 0, left = t, right = t;
-    Piece pc;
-    int64_t N = 1;
+    int j = 0, V = 1, start = 0, left = t, right = t;
+    Piece pc{};
+    int64_t N = 1, x_first = 0;
+    const T* fs = nullptr;
+    T* fd = nullptr;
     if (active) {
       pc = a.pieces[pidx];
       const RunDesc& d = a.runs[pc.run];
       k = load_coef<CT, Q>(d);
       N = d.N;
-      const int j = t - pc.t0;
-      const int V = pc.nthr;
+      j = t - pc.t0;
+      V = pc.nthr;
       const int mfull = pc.n - V * (S - 1);  // threads holding S sites; the rest hold S-1
       full = j < mfull;
       start = full ? j * S : mfull * S + (j - mfull) * (S - 1);
       left = pc.t0 + (j == 0 ? V - 1 : j - 1);
       right = pc.t0 + (j == V - 1 ? 0 : j + 1);
-      const T* fs = static_cast<const T*>(a.src.f) + d.off;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        if (s < S - 1 || full) {
-          const int64_t x = (pc.x0 + start + s) % N;
-#pragma unroll
-          for (int i = 0; i < Q; ++i) f[i][s] = to_compute(fs[(int64_t)i * a.src.plane + x], k.scale);
-        } else {
-#pragma unroll
-          for (int i = 0; i < Q; ++i) f[i][s] = CT(0);
-        }
-      }
+      x_first = (pc.x0 + j) % N;
+      fs = static_cast<const T*>(a.src.f) + d.off;
+      fd = static_cast<T*>(a.dst.f) + d.off;
     }
 
+    // ---- load: coalesced global reads of all planes into the staging area, then registers
+    const int sbase = pc.t0 * S;  // this piece's sites in each staged plane
+    if (active) {
+      int64_t x = x_first;
+      for (int li = j; li < pc.n; li += V) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) stage[i * NT * S + sbase + li] = to_compute(fs[(int64_t)i * a.src.plane + x], k.scale);
+        x += V;
+        while (x >= N) x -= N;
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int s = 0; s < S; ++s) f[i][s] = (s < S - 1 || full) ? stage[i * NT * S + sbase + start + s] : CT(0);
+    }
+    __syncthreads();
+
     for (int step = 0; step < a.ksteps; ++step) {
-      CT* xr = xR + (step & 1) * NX * NT;
-      CT* xl = xL + (step & 1) * NX * NT;
+      CT* const xr = xbase + (step & 1) * 2 * NX * NT;  // right-moving values leaving threads
+      CT* const xl = xr + NX * NT;                       // left-moving values leaving threads
       if (active) {
+        // A. per-site sums
+        CT acc[S], rho[S], rho2[S], tt[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          CT g[Q];
+          CT sg = f[0][s];
 #pragma unroll
-          for (int i = 0; i < Q; ++i) g[i] = f[i][s];
-          collide<Q, CT>(g, k);
-#pragma unroll
-          for (int i = 0; i < Q; ++i) f[i][s] = g[i];
+          for (int i = 1; i < Q; ++i) sg = add_rn(sg, f[i][s]);
+          acc[s] = sg;
+          rho[s] = add_rn(k.rhobar, sg);
+          rho2[s] = mul_rn(rho[s], rho[s]);
         }
-        // Values leaving the thread: the last c (c > 0) or first |c| (c < 0) held sites.
+        // B. plane by plane: collide, write to the destination site's register or send.
         StaticFor<1, Q>::run([&](auto ic) {
           constexpr int i = decltype(ic)::value;
           constexpr int c = speed(i);
           constexpr int kk = c > 0 ? c : -c;
           constexpr int base = kk * (kk - 1) / 2;
+          if constexpr (c > 0) {
 #pragma unroll
-          for (int jj = 0; jj < kk; ++jj) {
-            if constexpr (c > 0) xr[(base + jj) * NT + t] = full ? f[i][S - kk + jj] : f[i][S - 1 - kk + jj];
-            else xl[(base + jj) * NT + t] = f[i][jj];
+            for (int s = S - 1; s >= 0; --s) {
+              tt[s] = mul_rn(rho[s], k.a[i]);  // shared with the -c plane that follows
+              const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
+              acc[s] = add_rn(acc[s], -v);
+              if (s + kk <= S - 2) {
+                f[i][s + kk] = v;
+              } else if (s + kk == S - 1) {
+                if (full) f[i][S - 1] = v;
+                else xr[base * NT + t] = v;
+              } else if (s <= S - 2) {
+                xr[(base + (full ? s + kk - S : s + kk - S + 1)) * NT + t] = v;
+              } else if (full) {  // s == S - 1 holds a site only in threads with S sites
+                xr[(base + s + kk - S) * NT + t] = v;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+              const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
+              acc[s] = add_rn(acc[s], -v);
+              if (s >= kk) f[i][s - kk] = v;
+              else xl[(base + s) * NT + t] = v;
+            }
           }
         });
+#pragma unroll
+        for (int s = 0; s < S; ++s) f[0][s] = acc[s];
       }
       __syncthreads();
       if (active) {
+        // C. values entering from the neighbours
         StaticFor<1, Q>::run([&](auto ic) {
           constexpr int i = decltype(ic)::value;
           constexpr int c = speed(i);
           constexpr int kk = c > 0 ? c : -c;
           constexpr int base = kk * (kk - 1) / 2;
-          CT rv[kk];
-#pragma unroll
-          for (int jj = 0; jj < kk; ++jj)
-            rv[jj] = (c > 0) ? xr[(base + jj) * NT + left] : xl[(base + jj) * NT + right];
           if constexpr (c > 0) {
-            // f_i(x + c) <- f*_i(x): slot s takes slot s - c, the first c slots come from the left thread.
 #pragma unroll
-            for (int s = S - 1; s >= kk; --s) f[i][s] = f[i][s - kk];
-#pragma unroll
-            for (int s = 0; s < kk; ++s) f[i][s] = rv[s];
+            for (int jj = 0; jj < kk; ++jj) f[i][jj] = xr[(base + jj) * NT + left];
           } else {
-            // c < 0: slot s takes slot s + |c|; the last |c| held slots come from the right thread.
+            // threads with S sites fill slots S-kk .. S-1, threads with S-1 sites S-1-kk .. S-2
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-              if (s + kk < S - 1) {
-                f[i][s] = f[i][s + kk];
-              } else if (s + kk == S - 1) {
-                f[i][s] = full ? f[i][S - 1] : rv[0];
-              } else {
-                const int jf = s - (S - kk);  // source index when the thread holds S sites
-                const int js = jf + 1;        // ... and when it holds S - 1 (slot S-1 unused then)
-                f[i][s] = full ? rv[jf] : (js < kk ? rv[js < kk ? js : 0] : CT(0));
-              }
+            for (int jj = 0; jj < kk; ++jj) {
+              const CT v = xl[(base + jj) * NT + right];
+              if (full) f[i][S - kk + jj] = v;
+              else f[i][S - 1 - kk + jj] = v;
             }
           }
         });
       }
     }
+    __syncthreads();  // the last step's exchange reads finish before the staging area is reused
 
+    // ---- store: registers into the staging area, then coalesced global writes of all planes
     if (active) {
-      const RunDesc& d = a.runs[pc.run];
-      T* fd = static_cast<T*>(a.dst.f) + d.off;
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const int li = start + s;
-        if ((s < S - 1 || full) && li >= pc.st_lo && li < pc.st_hi) {
-          const int64_t x = (pc.x0 + li) % N;
+      for (int i = 0; i < Q; ++i)
 #pragma unroll
-          for (int i = 0; i < Q; ++i) from_compute(f[i][s], k.inv_scale, fd + (int64_t)i * a.dst.plane + x);
+        for (int s = 0; s < S; ++s)
+          if (s < S - 1 || full) stage[i * NT * S + sbase + start + s] = f[i][s];
+    }
+    __syncthreads();
+    if (active) {
+      int64_t x = x_first;
+      for (int li = j; li < pc.n; li += V) {
+        if (li >= pc.st_lo && li < pc.st_hi) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i)
+            from_compute(stage[i * NT * S + sbase + li], k.inv_scale, fd + (int64_t)i * a.dst.plane + x);
         }
+        x += V;
+        while (x >= N) x -= N;
       }
     }
+    __syncthreads();
   }
 }
 
 template <int Q, int ST, int S>
 size_t smem_bytes_t(int NT) {
   using CT = typename StorageType<ST>::compute;
-  constexpr int C = cmax_of(Q);
-  return sizeof(CT) * 2 * 2 * (C * (C + 1) / 2) * (size_t)NT;
+  return sizeof(CT) * (size_t)smem_elems_per_thread(Q, S) * (size_t)NT;
 }
 
 template <int Q, int ST, int S>
@@ -244,12 +295,6 @@ bool resident_supported(int Q, int storage, int S, int NT) {
   if (storage == kF64 && S > 8) return false;
   const int maxt = storage == kF64 ? 256 : (S <= 8 ? 512 : (S <= 12 ? 384 : 256));
   return NT >= 32 && NT <= maxt && NT % 32 == 0;
-}
-
-size_t resident_smem_bytes(int Q, int storage, int NT) {
-  const int C = (Q - 1) / 2;
-  const size_t es = storage == kF64 ? 8 : 4;
-  return es * 2 * 2 * (C * (C + 1) / 2) * (size_t)NT;
 }
 
 cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm) {
