@@ -187,6 +187,7 @@ def main():
     prec = {"f32": lb.F32, "f16s": lb.F16S, "f64": lb.F64}[args.precision]
     kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN}[args.kernel]
     opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
+                                 autotune=int(kern == lb.KERNEL_RESIDENT),
                                  stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
     desc = lb.lb_ks_describe(h)

@@ -95,6 +95,10 @@ typedef struct lb_ks_opts {
                                   F32/F16S; 4,6,8 for F64); 0 = auto */
     int32_t threads_per_block; /* resident kernel: 128, 256 or 512; 0 = auto */
     int32_t use_graph;         /* 1 (default): replay captured CUDA graphs for step sequences */
+    int32_t autotune;          /* resident kernel: 1 = at init, time a few tilings (sites per thread,
+                                  threads per block, split of the blocks between whole and
+                                  segmented lattices) on these lattices for a short run and keep
+                                  the fastest; 0 (default) = fixed defaults */
     void *stream;              /* cudaStream_t; NULL = legacy default stream */
 } lb_ks_opts;
 

@@ -50,7 +50,8 @@ class LbKsError(RuntimeError):
 class LbKsOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("dm_variant", C.c_int32), ("recentre_every", C.c_int32),
                 ("kernel", C.c_int32), ("steps_per_launch", C.c_int32), ("sites_per_thread", C.c_int32),
-                ("threads_per_block", C.c_int32), ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+                ("threads_per_block", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 _P = C.c_void_p

@@ -77,6 +77,7 @@ struct lb_ks {
   // resident kernel: lanes[0] rings (or segments if there are no rings), lanes[1] segments
   int S = 0, NT = 0, kmax = 0, kseg = 0, nlanes = 0;
   Lane lanes[2];
+  double tuned_weight = 0.0;  // lane split weight chosen by the autotuner (0 = not tuned)
   // scheduling
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -120,6 +121,18 @@ int dalloc(lb_ks* h, T** p, size_t count) {
   }
   h->allocations.push_back(*p);
   return LB_KS_OK;
+}
+
+template <typename T>
+void dfree(lb_ks* h, T** p) {
+  if (!*p) return;
+  for (size_t i = 0; i < h->allocations.size(); ++i)
+    if (h->allocations[i] == *p) {
+      h->allocations.erase(h->allocations.begin() + i);
+      break;
+    }
+  cudaFree(*p);
+  *p = nullptr;
 }
 
 Arena arena(lb_ks* h, int which) { return Arena{h->fbuf[which], h->plane}; }
@@ -243,14 +256,18 @@ int upload_lane(lb_ks* h, Lane* L, std::vector<Piece>& pieces, int NT, int k) {
 // cut into segments run k_seg-step launches (their halo grows with the steps per
 // launch).  When both kinds exist they run as two lanes on disjoint sets of blocks,
 // on two streams, sized so that both finish a chunk of steps at about the same time.
-int setup_resident(lb_ks* h, bool required) {
+// S_force / NT_force > 0 pin the tiling (autotuner trials); seg_weight is the relative
+// cost of a segment bundle against a ring bundle used to split the blocks between lanes.
+int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, double seg_weight = 1.25) {
   std::vector<int> cand;
-  if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
+  if (S_force) cand.push_back(S_force);
+  else if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
   else if (h->prec == kF64) cand = {8, 6, 4};
   else cand = {12, 8, 16, 6, 4};
   const int R = h->opts.recentre_every;
   for (int S : cand) {
-    const int NT = h->opts.threads_per_block ? h->opts.threads_per_block : default_threads(h->prec, S);
+    const int NT = NT_force ? NT_force
+                            : (h->opts.threads_per_block ? h->opts.threads_per_block : default_threads(h->prec, S));
     if (!resident_supported(h->Q, h->prec, S, NT)) continue;
     const int kring = h->opts.steps_per_launch ? h->opts.steps_per_launch : (R > 0 ? std::min(R, 1000) : 1000);
     int kseg = h->opts.steps_per_launch ? h->opts.steps_per_launch
@@ -280,13 +297,13 @@ int setup_resident(lb_ks* h, bool required) {
     } else {
       // Split the blocks: ring bundles take ceil(B1/G1) rounds of k_ring steps, segment
       // bundles ceil(B2/G2) rounds of the same steps plus their launch-edge and halo
-      // overhead (weighted 1.25).
+      // overhead (weight seg_weight, default 1.25, chosen by the autotuner if enabled).
       const int B1 = h->lanes[0].nbundles, B2 = h->lanes[1].nbundles;
       int best = 1;
       double bestT = 1e300;
       for (int G1 = 1; G1 < slots; ++G1) {
         const int G2 = slots - G1;
-        const double T = std::max<double>((B1 + G1 - 1) / G1, 1.25 * ((B2 + G2 - 1) / G2));
+        const double T = std::max<double>((B1 + G1 - 1) / G1, seg_weight * ((B2 + G2 - 1) / G2));
         if (T < bestT) { bestT = T; best = G1; }
       }
       h->lanes[0].grid = std::min(B1, best);
@@ -426,6 +443,76 @@ int run_chunk_graph(lb_ks* h, int64_t n) {
   h->graphs.push_back(ge);
   LBKS_CUDA(h, cudaGraphLaunch(exec, h->stream), "graph launch");
   h->launches += nk;
+  return LB_KS_OK;
+}
+
+void release_lanes(lb_ks* h) {
+  for (Lane& L : h->lanes) {
+    dfree(h, &L.d_pieces);
+    dfree(h, &L.d_bundles);
+    dfree(h, &L.d_queue);
+    L = Lane{};
+  }
+  h->nlanes = 0;
+}
+
+// Autotuner of the resident kernel: times a few tilings (sites per thread, threads per
+// block) and lane splits on this handle's own lattices for a short run, and keeps the
+// fastest.  Runs before the state is initialised, on the zeroed arenas (the kernel's
+// work does not depend on the values).
+int autotune_resident(lb_ks* h) {
+  struct Cand { int S, NT; double w; };
+  std::vector<Cand> cands;
+  std::vector<std::pair<int, int>> tilings;
+  if (h->opts.sites_per_thread) {
+    tilings.push_back({h->opts.sites_per_thread, h->opts.threads_per_block});
+  } else if (h->prec == kF64) {
+    tilings = {{8, 256}, {6, 256}, {4, 256}};
+  } else {
+    tilings = {{12, 384}, {16, 256}, {8, 512}};
+  }
+  for (auto& tl : tilings)
+    for (double w : {1.0, 1.3, 1.7}) cands.push_back({tl.first, tl.second, w});
+  const int64_t trial = std::max(2 * h->kseg, 100);
+  cudaEvent_t e0, e1;
+  LBKS_CUDA(h, cudaEventCreate(&e0), "tuner event");
+  LBKS_CUDA(h, cudaEventCreate(&e1), "tuner event");
+  double best_ms = 1e300;
+  Cand best = cands.front();
+  int rc = LB_KS_OK;
+  for (const Cand& c : cands) {
+    release_lanes(h);
+    if (setup_resident(h, false, c.S, c.NT, c.w) != LB_KS_OK) { cudaGetLastError(); continue; }
+    if (h->nlanes < 2 && c.w != 1.0) continue;  // the split weight only matters with two lanes
+    int64_t nk = 0;
+    for (int rep = 0; rep < 2 && rc == LB_KS_OK; ++rep) {  // first repetition warms up
+      cudaEventRecord(e0, h->stream);
+      rc = issue_steps(h, trial, h->stream, &nk);
+      cudaEventRecord(e1, h->stream);
+    }
+    if (rc != LB_KS_OK) break;
+    cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce != cudaSuccess) { rc = cuda_fail(h, ce, "tuner timing"); break; }
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LB_KS_OK) return rc;
+  release_lanes(h);
+  if (best_ms < 1e300) {
+    if ((rc = setup_resident(h, true, best.S, best.NT, best.w)) != LB_KS_OK) return rc;
+    h->tuned_weight = best.w;
+  } else if ((rc = setup_resident(h, true)) != LB_KS_OK) {
+    return rc;
+  }
+  // the trials advanced the (zero) state: start the real run from the first arena
+  h->cur = 0;
+  h->steps_done = 0;
+  h->phase = 0;
+  h->launches = 0;
+  LBKS_CUDA(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream), "clear flags");
   return LB_KS_OK;
 }
 
@@ -597,11 +684,12 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     return bail(cuda_fail(h, ce, "stream kernel setup"));
   if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "create capture stream"));
-  if (h->nlanes == 2) {
+  if (kern == LB_KS_KERNEL_RESIDENT) {
     if ((ce = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess)
       return bail(cuda_fail(h, ce, "create lane stream"));
+    if (o.autotune && (rc = autotune_resident(h)) != LB_KS_OK) return bail(rc);
   }
 
   // f = f^eq(rho0).
