@@ -59,6 +59,40 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(base: int, rank: int, nruns: int) -> int:
+    """First PCG64 seed of this rank's ensemble: ranks draw disjoint runs (weak scaling)."""
+    return base + rank * nruns
+
+
+def max_over_ranks(value: float, ws: int, device: str = "cuda") -> float:
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, ws: int, device: str = "cuda") -> float:
+    """Sum over all ranks (each rank's ensemble has its own total of sites)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(total_updates: float, max_ms: float) -> float:
+    """Site-updates per second of the whole job: all ranks' updates over the slowest rank's time."""
+    return total_updates / (max_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
 
@@ -180,9 +214,10 @@ def main():
     lbbuild.build()
     stream = torch.cuda.Stream()
     if args.workload == "long":
-        wl = workloads.long_lattice(seed=workloads.BASE_SEED + rank)
+        wl = workloads.long_lattice(seed=rank_seed(workloads.BASE_SEED, rank, 1))
     else:
-        wl = workloads.ensemble(nruns=args.nruns, nmax=args.nmax, seed=workloads.BASE_SEED + rank * args.nruns)
+        wl = workloads.ensemble(nruns=args.nruns, nmax=args.nmax,
+                                seed=rank_seed(workloads.BASE_SEED, rank, args.nruns))
     Q = wl.scheme
     prec = {"f32": lb.F32, "f16s": lb.F16S, "f64": lb.F64}[args.precision]
     kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN}[args.kernel]
@@ -215,13 +250,9 @@ def main():
         clocks = clk.stop()
         launches = lb.lb_ks_launches(h) - launches0
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), ws)
     updates = sites * LB_STEPS_PER_STEP * args.steps
-    value = updates * ws / (total_ms * 1e-3)
+    value = whole_job_rate(sum_over_ranks(updates, ws), total_ms)
 
     # Roofline of the dominant kernel.
     k = desc["steps_per_launch"]
