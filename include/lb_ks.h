@@ -149,6 +149,26 @@ LB_KS_API int lb_ks_batch_init(lb_ks_t **h, int scheme, int32_t nruns, const int
                      const double *dt, const double *tau, const double *rho0, const lb_ks_opts *opts);
 
 /*
+ * Create a handle for nruns lattices with fixed-value ends, the boundary of the
+ * travelling-front test of Sec. 3 (Table 5): run r has N[r] nodes
+ * X_j = j L[r] / (N[r] - 1), j = 0 .. N[r]-1, on [0, L[r]]; the end nodes and
+ * c_max ghost nodes beyond each end are held at f^eq(rho_left[r]) (j <= 0) and
+ * f^eq(rho_right[r]) (j >= N[r]-1) every step, so populations streaming in
+ * from outside carry the boundary state and those streaming out are dropped.
+ * rho0 (sum N[r] values, host or device) initialises the nodes; its two end
+ * values are replaced by the boundary values.  These lattices run on the plain
+ * kernel family (each node pulls plane i from node j - c_i); the guard's
+ * re-centring is not allowed (mass flows through the ends: recentre_every must
+ * be 0); lb_ks_rho and lb_ks_mass_energy cover the N[r] nodes.
+ * Errors: as lb_ks_batch_init, plus LB_KS_EINVAL for NULL or non-finite
+ * boundary values, opts->kernel STREAM/RESIDENT, or recentre_every != 0.
+ */
+LB_KS_API int lb_ks_batch_init_reservoir(lb_ks_t **h, int scheme, int32_t nruns, const int64_t *N,
+                                         const double *L, const double *dt, const double *tau,
+                                         const double *rho0, const double *rho_left, const double *rho_right,
+                                         const lb_ks_opts *opts);
+
+/*
  * Advance every run of the handle by n >= 0 time steps of
  * Eq. LB_equation_ordinary (each step: rho = sum_i f_i, f^eq, BGK collision,
  * periodic shift of f_i by c_i).  Asynchronous on the handle's stream.

@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "LbKsError", "LbKsOpts", "lb_ks_default_opts", "lb_ks_params", "lb_ks_tau_fit", "lb_ks_init",
-    "lb_ks_batch_init", "lb_ks_step", "lb_ks_rho", "lb_ks_mass_energy", "lb_ks_state_bytes", "lb_ks_save",
+    "lb_ks_batch_init", "lb_ks_batch_init_reservoir", "lb_ks_step", "lb_ks_rho", "lb_ks_mass_energy", "lb_ks_state_bytes", "lb_ks_save",
     "lb_ks_load", "lb_ks_steps_done", "lb_ks_describe", "lb_ks_launches", "lb_ks_fma_peak",
     "lb_ks_mass_energy_noalloc", "lb_ks_free",
     "lb_ks_last_error", "library_path", "D1Q5", "D1Q7", "F64", "F32", "F16S", "KERNEL_AUTO", "KERNEL_PLAIN",
@@ -64,6 +64,8 @@ ABI_FUNCTIONS = {
     "lb_ks_init": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int64, C.c_double, C.c_double, C.c_double, _P,
                              C.POINTER(LbKsOpts)]),
     "lb_ks_batch_init": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int32, _P, _P, _P, _P, _P, C.POINTER(LbKsOpts)]),
+    "lb_ks_batch_init_reservoir": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int32, _P, _P, _P, _P, _P, _P, _P,
+                                             C.POINTER(LbKsOpts)]),
     "lb_ks_step": (C.c_int, [_P, C.c_int64]),
     "lb_ks_rho": (C.c_int, [_P, _P]),
     "lb_ks_mass_energy": (C.c_int, [_P, _P, _P]),
@@ -166,6 +168,17 @@ def lb_ks_batch_init(scheme: int, N, L, dt, tau, rho0, opts: LbKsOpts | None = N
     h = C.c_void_p()
     rc = _load().lb_ks_batch_init(C.byref(h), scheme, len(N), _ptr(N, np.int64), _ptr(L), _ptr(dt), _ptr(tau),
                                   _ptr(rho0), C.byref(opts) if opts is not None else None)
+    _check(rc)
+    return h
+
+
+def lb_ks_batch_init_reservoir(scheme: int, N, L, dt, tau, rho0, rho_left, rho_right, opts: LbKsOpts | None = None):
+    N = np.ascontiguousarray(N, dtype=np.int64)
+    L, dt, tau, rl, rr = (np.ascontiguousarray(v, dtype=np.float64) for v in (L, dt, tau, rho_left, rho_right))
+    h = C.c_void_p()
+    rc = _load().lb_ks_batch_init_reservoir(C.byref(h), scheme, len(N), _ptr(N, np.int64), _ptr(L), _ptr(dt),
+                                            _ptr(tau), _ptr(rho0), _ptr(rl), _ptr(rr),
+                                            C.byref(opts) if opts is not None else None)
     _check(rc)
     return h
 

@@ -52,6 +52,7 @@ struct Lane {
 
 struct lb_ks {
   int Q = 0, prec = 0, kernel = 0, cmax = 0;
+  bool reservoir = false;  // lattices with fixed-value ends instead of periodic ones
   lb_ks_opts opts{};
   int32_t nruns = 0;
   std::vector<int64_t> N, rho_off;
@@ -382,7 +383,10 @@ int issue_steps(lb_ks* h, int64_t n, cudaStream_t s, int64_t* nk) {
       }
       h->cur = to;
     } else {
-      if (h->kernel == LB_KS_KERNEL_STREAM) {
+      if (h->reservoir) {
+        LBKS_CUDA(h, launch_reservoir_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
+                                           h->d_plain_tiles, h->n_plain_tiles, 0, s), "reservoir step");
+      } else if (h->kernel == LB_KS_KERNEL_STREAM) {
         LBKS_CUDA(h, launch_stream_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
                                         h->d_stream_tiles, h->n_stream_tiles, s), "stream step");
       } else {
@@ -527,9 +531,21 @@ int check_flags(lb_ks* h) {
 }
 
 int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const double* L, const double* dt,
-           const double* tau, const double* rho0, const lb_ks_opts* opts) {
+           const double* tau, const double* rho0, const lb_ks_opts* opts, const double* rho_left = nullptr,
+           const double* rho_right = nullptr) {
   if (!out) return fail(nullptr, LB_KS_EINVAL, "h must not be NULL");
   *out = nullptr;
+  const bool reservoir = rho_left != nullptr;
+  if (reservoir) {
+    if (!rho_right) return fail(nullptr, LB_KS_EINVAL, "rho_left and rho_right must both be given");
+    for (int32_t r = 0; r < nruns; ++r)
+      if (!std::isfinite(rho_left[r]) || !std::isfinite(rho_right[r]))
+        return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": reservoir values must be finite");
+    if (opts && (opts->kernel == LB_KS_KERNEL_STREAM || opts->kernel == LB_KS_KERNEL_RESIDENT))
+      return fail(nullptr, LB_KS_EINVAL, "reservoir ends run on the plain kernel family only");
+    if (opts && opts->recentre_every != 0)
+      return fail(nullptr, LB_KS_EINVAL, "reservoir ends exchange mass: recentre_every must be 0");
+  }
   if (scheme != LB_KS_D1Q5 && scheme != LB_KS_D1Q7) return fail(nullptr, LB_KS_EINVAL, "scheme must be 5 or 7");
   if (nruns < 1) return fail(nullptr, LB_KS_EINVAL, "nruns must be >= 1");
   if (!N || !L || !dt || !tau || !rho0) return fail(nullptr, LB_KS_EINVAL, "NULL argument");
@@ -585,7 +601,8 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     RunDesc& d = h->runs_h[r];
     std::memset(&d, 0, sizeof(d));
     double A[7], B[7];
-    const double dx = L[r] / (double)N[r];
+    // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
+    const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
     if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK)
       return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
     double mass = 0.0;
@@ -606,8 +623,12 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     }
     const double scale = (o.precision == kF16S && gmax > 0.0) ? gmax : 1.0;
     const double w = 1.0 / tau[r];
-    d.off = off;
+    const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
+    d.off = off + ghost;
     d.N = N[r];
+    d.reservoir = reservoir ? 1 : 0;
+    d.rho_left = reservoir ? rho_left[r] : 0.0;
+    d.rho_right = reservoir ? rho_right[r] : 0.0;
     for (int i = 0; i < scheme; ++i) {
       d.A[i] = A[i];
       d.B[i] = B[i];
@@ -624,7 +645,7 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     d.rhobarf = (float)d.rhobar;
     d.scalef = (float)scale;
     d.inv_scalef = (float)(1.0 / scale);
-    off += align_up(N[r], kAlign);
+    off += align_up(N[r] + 2 * ghost, kAlign);
   }
   h->plane = std::max<int64_t>(off, kAlign);
 
@@ -633,7 +654,10 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   std::vector<int32_t> st_begin(nruns + 1);
   const int TS = stream_tile_sites();
   for (int32_t r = 0; r < nruns; ++r) {
-    for (int64_t x = 0; x < N[r]; x += kPlainTile) pt.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(kPlainTile, N[r] - x), 0});
+    // reservoir lattices: the plain-family tiles also cover the ghost nodes
+    const int64_t g0 = reservoir ? -cmax : 0, g1 = reservoir ? N[r] + cmax : N[r];
+    for (int64_t x = g0; x < g1; x += kPlainTile)
+      pt.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(kPlainTile, g1 - x), 0});
     st_begin[r] = (int32_t)st.size();
     for (int64_t x = 0; x < N[r]; x += TS) st.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(TS, N[r] - x), 0});
   }
@@ -674,7 +698,10 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
 
   // Kernel family.
   int kern = o.kernel;
-  if (kern == LB_KS_KERNEL_AUTO || kern == LB_KS_KERNEL_RESIDENT) {
+  h->reservoir = reservoir;
+  if (reservoir) {
+    kern = LB_KS_KERNEL_PLAIN;
+  } else if (kern == LB_KS_KERNEL_AUTO || kern == LB_KS_KERNEL_RESIDENT) {
     rc = setup_resident(h, kern == LB_KS_KERNEL_RESIDENT);
     if (rc < 0) return bail(rc);
     kern = rc == 0 ? LB_KS_KERNEL_RESIDENT : (h->prec == kF64 ? LB_KS_KERNEL_PLAIN : LB_KS_KERNEL_STREAM);
@@ -697,6 +724,13 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
                            h->d_rho_off, h->stream)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "init"));
   h->launches += 1;
+  if (reservoir) {  // end nodes and ghosts at f^eq(rho_bc)
+    for (int b = 0; b < 2; ++b)
+      if ((ce = launch_reservoir_step(scheme, h->prec, arena(h, b), arena(h, b), h->d_runs, h->d_plain_tiles,
+                                      h->n_plain_tiles, 1, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(h, ce, "reservoir init"));
+    h->launches += 2;
+  }
   if ((ce = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, ce, "init sync"));
   *out = h;
   return LB_KS_OK;
@@ -725,6 +759,16 @@ int lb_ks_init(lb_ks_t** h, int scheme, int64_t N, double L, double dt, double t
 int lb_ks_batch_init(lb_ks_t** h, int scheme, int32_t nruns, const int64_t* N, const double* L, const double* dt,
                      const double* tau, const double* rho0, const lb_ks_opts* opts) {
   return create(h, scheme, nruns, N, L, dt, tau, rho0, opts);
+}
+
+int lb_ks_batch_init_reservoir(lb_ks_t** h, int scheme, int32_t nruns, const int64_t* N, const double* L,
+                               const double* dt, const double* tau, const double* rho0, const double* rho_left,
+                               const double* rho_right, const lb_ks_opts* opts) {
+  if (!rho_left || !rho_right) {
+    if (h) *h = nullptr;
+    return fail(nullptr, LB_KS_EINVAL, "rho_left and rho_right must not be NULL");
+  }
+  return create(h, scheme, nruns, N, L, dt, tau, rho0, opts, rho_left, rho_right);
 }
 
 int lb_ks_step(lb_ks_t* h, int64_t n) {

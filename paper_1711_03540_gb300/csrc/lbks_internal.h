@@ -27,6 +27,11 @@ struct RunDesc {
   double r, rhobar, scale, inv_scale;  // scale: F16S stored value = g / scale
   float af[8], bf[8];
   float rf, rhobarf, scalef, inv_scalef;
+  // Fixed-value ends (front test of Table 5): nodes j <= 0 and j >= N-1, and c_max ghost
+  // nodes beyond each end (stored at j = -c_max..-1 and N..N-1+c_max), are reservoirs
+  // held at f^eq(rho_left) / f^eq(rho_right).  reservoir = 0: periodic lattice.
+  int32_t reservoir, pad_;
+  double rho_left, rho_right;
 };
 
 // One unit of work of the resident kernel: a lattice (ring) or a stretch of
@@ -63,6 +68,10 @@ cudaError_t launch_plain_step(int Q, int storage, Arena src, Arena dst, const Ru
                               const Tile* tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_stream_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
                                const Tile* tiles, int ntiles, cudaStream_t s);
+// Lattices with reservoir ends: tiles cover nodes -c_max .. N-1+c_max.  reset_only = 1
+// writes f^eq(rho_bc) into the reservoir nodes of dst and nothing else (initial state).
+cudaError_t launch_reservoir_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
+                                  const Tile* tiles, int ntiles, int reset_only, cudaStream_t s);
 // Guard: per-tile FP64 partial sums of rho and rho^2 (scratch: 2 doubles per tile),
 // then per-run totals, non-finite flag, and (if recentre) g_0 += (M0 - M)/N.
 cudaError_t launch_mass_partials(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles,

@@ -76,6 +76,46 @@ __global__ void __launch_bounds__(kPlainThreads) plain_step_kernel(Arena src, Ar
     from_compute(g[i], k.inv_scale, fd + (int64_t)i * dst.plane + wrap_site(x + speed(i), d.N));
 }
 
+// Lattices with reservoir ends (the fixed end values of the front test, Table 5).
+// One thread per node j in [-c_max, N + c_max): reservoir nodes (j <= 0, j >= N-1,
+// ghosts included) are set to f^eq(rho_bc); an interior node pulls plane i from node
+// j - c_i, recomputing that node's collision with the same collide() as every other
+// kernel, so the values are those a push from j - c_i would deliver.
+template <int Q, int ST>
+__global__ void __launch_bounds__(kPlainThreads) reservoir_step_kernel(Arena src, Arena dst,
+                                                                       const RunDesc* __restrict__ runs,
+                                                                       const Tile* __restrict__ tiles, int reset_only) {
+  using T = typename StorageType<ST>::type;
+  using CT = typename StorageType<ST>::compute;
+  const Tile tl = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= tl.len) return;
+  const RunDesc& d = runs[tl.run];
+  const int64_t j = (int64_t)tl.x0 + threadIdx.x;
+  T* fd = static_cast<T*>(dst.f) + d.off;
+  if (j <= 0 || j >= d.N - 1) {
+    const double rb = j <= 0 ? d.rho_left : d.rho_right;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double v = __fma_rn(d.B[i], __dmul_rn(rb, rb), __dmul_rn(d.A[i], rb));
+      if (i == 0) v = __dsub_rn(v, d.rhobar);
+      from_compute(static_cast<CT>(v), static_cast<CT>(d.inv_scale), fd + (int64_t)i * dst.plane + j);
+    }
+    return;
+  }
+  if (reset_only) return;
+  const T* fs = static_cast<const T*>(src.f) + d.off;
+  const Coef<CT, Q> k = load_coef<CT, Q>(d);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int64_t y = j - speed(i);
+    CT g[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) g[q] = to_compute(fs[(int64_t)q * src.plane + y], k.scale);
+    collide<Q, CT>(g, k);
+    from_compute(g[i], k.inv_scale, fd + (int64_t)i * dst.plane + j);
+  }
+}
+
 // Error-free sum: s + e == a + b exactly (Knuth's TwoSum, six rounded operations).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -283,6 +323,14 @@ cudaError_t launch_plain_step(int Q, int storage, Arena src, Arena dst, const Ru
   if (ntiles == 0) return cudaSuccess;
   if (storage == kF16S) return cudaErrorInvalidValue;
   LBKS_DISPATCH_Q_ST(Q, storage, (plain_step_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, dst, runs, tiles)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reservoir_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
+                                  int ntiles, int reset_only, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  LBKS_DISPATCH_Q_ST(Q, storage, (reservoir_step_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(
+                                     src, dst, runs, tiles, reset_only)));
   return cudaGetLastError();
 }
 

@@ -99,6 +99,15 @@ def test_init_rejects_invalid_arguments(lb, bad):
     assert lb.lb_ks_last_error(None) not in ("", "no error")
 
 
+@pytest.mark.parametrize("bad", [dict(kernel=2), dict(kernel=3), dict(recentre_every=10), dict(rho_left=np.nan)])
+def test_reservoir_init_rejects_invalid_arguments(lb, bad):
+    opts = lb.lb_ks_default_opts(**{k: v for k, v in bad.items() if k != "rho_left"})
+    rl = bad.get("rho_left", 1.8)
+    with pytest.raises(lb.LbKsError) as e:
+        lb.lb_ks_batch_init_reservoir(7, [101], [60.0], [1e-4], [1.0], np.zeros(101), [rl], [4.2], opts)
+    assert e.value.code == -1
+
+
 def test_no_device_is_an_error_not_a_fallback(lb):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

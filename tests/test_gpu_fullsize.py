@@ -1,0 +1,110 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times.
+
+* The 4096-lattice D1Q7 ensemble (9.38 M sites), FP32 storage, guard every 500
+  steps, autotuned resident kernel: 16 evenly spaced lattices are recomputed by
+  the FP64 oracle; each must agree to rel-L2 <= 1e-4 (the FP32 tolerance the
+  method is held to over T <= 10).  FP64 plain kernel on the same ensemble:
+  the same lattices to 1e-12 relative.
+* The 2^24-site lattice (too long for the oracle): properties that hold at any
+  size -- translation by an integer number of sites commutes with the step
+  (bitwise: every site does the same arithmetic, also across segment cuts),
+  the resident (segmented) and streaming kernels agree bitwise, and the FP64
+  guard keeps the mass.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbks as ora
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_03540_gb300 import build
+
+    build.build()
+    import paper_1711_03540_gb300 as lb
+
+    return lb
+
+
+@pytest.fixture(scope="module")
+def ensemble():
+    from paper_1711_03540_gb300 import workloads
+
+    return workloads.ensemble()
+
+
+def _run(lb, wl, n, rho0=None, **opts):
+    r0 = wl.rho0 if rho0 is None else rho0
+    h = lb.lb_ks_batch_init(wl.scheme, wl.N, wl.L, wl.dt, wl.tau, r0, lb.lb_ks_default_opts(**opts))
+    try:
+        lb.lb_ks_step(h, n)
+        out = np.empty(r0.size)
+        lb.lb_ks_rho(h, out)
+        m = np.empty(wl.nruns)
+        lb.lb_ks_mass_energy(h, m, None)
+        d = lb.lb_ks_describe(h)
+    finally:
+        lb.lb_ks_free(h)
+    return out, m, d
+
+
+def _sample(wl, out, n, k=16):
+    idx = np.linspace(0, wl.nruns - 1, k).astype(int)
+    sub = wl.subset(idx)
+    ref, _ = ora.run_batch(sub.scheme, sub.N, sub.L / sub.N, sub.dt, sub.tau, sub.rho0, n, nthreads=16)
+    off = wl.offsets()
+    got = np.concatenate([out[off[i]:off[i + 1]] for i in idx])
+    so = sub.offsets()
+    return [(got[so[j]:so[j + 1]], ref[so[j]:so[j + 1]]) for j in range(k)]
+
+
+def test_bench_configuration_fp32_sampled_against_oracle(lb, ensemble):
+    n = 1000
+    out, m, d = _run(lb, ensemble, n, precision=1, recentre_every=500, kernel=3, autotune=1)
+    assert d["kernel"] == 3 and d["nruns"] == 4096
+    for got, ref in _sample(ensemble, out, n):
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-4
+    m0 = np.array([ensemble.run(i).sum() for i in range(ensemble.nruns)])
+    assert np.all(np.abs(m - m0) <= 1e-6 * np.sqrt(ensemble.N))
+
+
+def test_bench_ensemble_fp64_plain_sampled_against_oracle(lb, ensemble):
+    n = 300
+    out, _, d = _run(lb, ensemble, n, precision=0, kernel=1)
+    assert d["kernel"] == 1
+    for got, ref in _sample(ensemble, out, n):
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.fixture(scope="module")
+def long_lattice():
+    from paper_1711_03540_gb300 import workloads
+
+    return workloads.long_lattice()
+
+
+def test_long_lattice_families_and_mass(lb, long_lattice):
+    wl, n = long_lattice, 200
+    a, ma, d = _run(lb, wl, n, precision=1, kernel=3, recentre_every=100)
+    assert d["kernel"] == 3 and d["total_sites"] == 1 << 24
+    c, _, _ = _run(lb, wl, n, precision=1, kernel=2, recentre_every=100)
+    np.testing.assert_array_equal(a, c)
+    assert abs(ma[0] - wl.rho0.sum()) <= 1e-6 * np.sqrt(wl.sites)
+
+
+def test_long_lattice_translation_bitwise(lb, long_lattice):
+    # FP64 storage (no stored mean offset, whose summation order would depend on the
+    # rotation) and no guard (its residual carrying walks tiles anchored at site 0);
+    # the resident kernel cuts this lattice into thousands of haloed segments.
+    wl, n, shift = long_lattice, 200, 12345
+    a, _, d = _run(lb, wl, n, precision=0, kernel=3)
+    assert d["kernel"] == 3
+    b, _, _ = _run(lb, wl, n, rho0=np.roll(wl.rho0, shift), precision=0, kernel=3)
+    np.testing.assert_array_equal(np.roll(a, shift), b)

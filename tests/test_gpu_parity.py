@@ -163,6 +163,18 @@ def test_fp32_error_against_oracle(lb, kern):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) <= bound
 
 
+def test_printed_delta_m_variant_matches_oracle_and_differs(lb):
+    """The printed reading of Eq. delta_M is kept as an option: the GPU follows the
+    oracle with the same reading, and the two readings differ once tau != 1."""
+    N, L, dt, tau, n = 400, 40.0, 1e-4, 2.0, 500
+    r0 = two_harmonic(N, L)
+    ref_p = ora.run(7, r0, L / N, dt, tau, n, dm_variant=ora.DM_PRINTED)
+    ref_d = ora.run(7, r0, L / N, dt, tau, n)
+    out_p, _ = run_gpu(lb, 7, N, L, dt, tau, r0, n, dm_variant=1, kernel=3)
+    assert np.max(np.abs(out_p - ref_p)) <= 1e-12 * np.abs(ref_p).max()
+    assert np.max(np.abs(ref_p - ref_d)) > 1e-9 * np.abs(ref_d).max()
+
+
 def test_zero_steps_returns_initial_density(lb):
     r0 = two_harmonic(100)
     for prec in (0, 1):
