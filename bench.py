@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--kernel", default="resident", choices=["resident", "stream", "plain"])
     p.add_argument("--precision", default="f32", choices=["f32", "f16s", "f64"])
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="fixed default tiling (deterministic launch sequence, for profiling)")
     return p.parse_args()
 
 
@@ -222,7 +224,7 @@ def main():
     prec = {"f32": lb.F32, "f16s": lb.F16S, "f64": lb.F64}[args.precision]
     kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN}[args.kernel]
     opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
-                                 autotune=int(kern == lb.KERNEL_RESIDENT),
+                                 autotune=int(kern == lb.KERNEL_RESIDENT and not args.no_autotune),
                                  stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
     desc = lb.lb_ks_describe(h)
