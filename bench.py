@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
     p.add_argument("--no-autotune", action="store_true",
                    help="fixed default tiling (deterministic launch sequence, for profiling)")
+    p.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
+                   help="resident work group for whole lattices: 1 block, a 2-block cluster, 0 = auto")
     return p.parse_args()
 
 
@@ -225,7 +227,7 @@ def main():
     kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN}[args.kernel]
     opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
                                  autotune=int(kern == lb.KERNEL_RESIDENT and not args.no_autotune),
-                                 stream=stream)
+                                 cluster_size=args.cluster, stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
     desc = lb.lb_ks_describe(h)
     sites = wl.sites
@@ -300,7 +302,7 @@ def main():
                        "lb_steps_per_step": LB_STEPS_PER_STEP, "storage": args.precision + " (f_0 stored as deviation)",
                        "guard_every": 0 if prec == lb.F64 else GUARD_EVERY, "kernel": args.kernel,
                        "sites_per_thread": desc["sites_per_thread"], "threads_per_block": desc["threads_per_block"],
-                       "steps_per_launch": k,
+                       "steps_per_launch": k, "cluster_size": desc["cluster_size"],
                        "l2": f"state {sites * Q * elem / 1e6:.0f} MB > 129 MB L2 (no flush needed)"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches)}
 

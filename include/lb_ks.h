@@ -55,7 +55,8 @@ extern "C" {
 #define LB_KS_ENOMEM (-2)    /* device or host allocation failed */
 #define LB_KS_ECUDA (-3)     /* CUDA runtime error, or no usable device */
 #define LB_KS_EUNSTABLE (-4) /* non-finite FP64 mass found at a guard step (sticky) */
-#define LB_KS_ETIMEOUT (-5)  /* reserved: a bounded device wait ran out (sticky) */
+#define LB_KS_ETIMEOUT (-5)  /* a bounded device wait ran out (sticky): the two blocks of a
+                                resident cluster stopped exchanging values (an internal error) */
 
 /* Lattice schemes (Sec. 2.3): the number of speeds. */
 #define LB_KS_D1Q5 5
@@ -100,6 +101,11 @@ typedef struct lb_ks_opts {
                                   segmented lattices) on these lattices for a short run and keep
                                   the fastest; 0 (default) = fixed defaults */
     void *stream;              /* cudaStream_t; NULL = legacy default stream */
+    int32_t cluster_size;      /* resident kernel, whole lattices: blocks per work group.  1 = one
+                                  thread block; 2 = a cluster of two blocks (distributed shared
+                                  memory), which holds lattices of up to 2 x threads x sites per
+                                  thread whole instead of cutting them into segments; 0 (default)
+                                  = 2 when some lattice needs it, else 1 (the autotuner tries both) */
 } lb_ks_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -214,11 +220,12 @@ LB_KS_API int64_t lb_ks_steps_done(const lb_ks_t *h);
 
 /*
  * Describe the handle: kernel family actually used (LB_KS_KERNEL_*), resident
- * sites per thread, threads per block and steps per launch (0 when not
- * resident), number of runs and total sites.  Any pointer may be NULL.
+ * sites per thread, threads per block, steps per launch and blocks per work group
+ * of whole lattices (1 or 2; all 0 when not resident), number of runs and total
+ * sites.  Any pointer may be NULL.
  */
 LB_KS_API int lb_ks_describe(const lb_ks_t *h, int *kernel, int *sites_per_thread, int *threads_per_block,
-                   int *steps_per_launch, int32_t *nruns, int64_t *total_sites);
+                   int *steps_per_launch, int *cluster_size, int32_t *nruns, int64_t *total_sites);
 
 /* Kernel launches issued by this handle since creation (a counter kept on the host). */
 LB_KS_API int64_t lb_ks_launches(const lb_ks_t *h);

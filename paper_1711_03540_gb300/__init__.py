@@ -51,7 +51,7 @@ class LbKsOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("dm_variant", C.c_int32), ("recentre_every", C.c_int32),
                 ("kernel", C.c_int32), ("steps_per_launch", C.c_int32), ("sites_per_thread", C.c_int32),
                 ("threads_per_block", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("cluster_size", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -74,7 +74,7 @@ ABI_FUNCTIONS = {
     "lb_ks_load": (C.c_int, [_P, _P, C.c_size_t]),
     "lb_ks_steps_done": (C.c_int64, [_P]),
     "lb_ks_describe": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                 C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+                                 C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
     "lb_ks_launches": (C.c_int64, [_P]),
     "lb_ks_fma_peak": (C.c_int, [C.c_int, _PD]),
     "lb_ks_mass_energy_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int64, C.c_int64, C.c_double, C.c_double, _P,
@@ -214,11 +214,12 @@ def lb_ks_steps_done(h) -> int:
 
 
 def lb_ks_describe(h) -> dict:
-    k, s, t, l = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    k, s, t, l, cl = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
     nr, tot = C.c_int32(), C.c_int64()
-    _check(_load().lb_ks_describe(h, C.byref(k), C.byref(s), C.byref(t), C.byref(l), C.byref(nr), C.byref(tot)), h)
+    _check(_load().lb_ks_describe(h, C.byref(k), C.byref(s), C.byref(t), C.byref(l), C.byref(cl), C.byref(nr),
+                                  C.byref(tot)), h)
     return {"kernel": k.value, "sites_per_thread": s.value, "threads_per_block": t.value,
-            "steps_per_launch": l.value, "nruns": nr.value, "total_sites": tot.value}
+            "steps_per_launch": l.value, "cluster_size": cl.value, "nruns": nr.value, "total_sites": tot.value}
 
 
 def lb_ks_launches(h) -> int:

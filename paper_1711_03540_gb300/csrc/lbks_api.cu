@@ -42,6 +42,8 @@ size_t storage_bytes(int prec) { return prec == kF64 ? 8 : (prec == kF32 ? 4 : 2
 // One resident-kernel work list: bundles of pieces, launched k steps at a time on `grid` blocks.
 struct Lane {
   bool segmented = false;
+  int cl = 1;           // blocks per work group (2: thread block clusters)
+  double weight = 1.0;  // cost of a bundle relative to a single-block ring bundle (grid split)
   int k = 0, grid = 0, nbundles = 0;
   Piece* d_pieces = nullptr;
   int2* d_bundles = nullptr;
@@ -75,15 +77,17 @@ struct lb_ks {
   double* d_energy = nullptr;
   double* d_delta = nullptr;
   int* d_flags = nullptr;
-  // resident kernel: lanes[0] rings (or segments if there are no rings), lanes[1] segments
+  // resident kernel: up to three lanes, whole lattices first (one block, then cluster
+  // pairs), segmented lattices last
   int S = 0, NT = 0, kmax = 0, kseg = 0, nlanes = 0;
-  Lane lanes[2];
+  Lane lanes[3];
   double tuned_weight = 0.0;  // lane split weight chosen by the autotuner (0 = not tuned)
+  int tuned_cl = 0;           // ring work-group size chosen by the autotuner (0 = not tuned)
   // scheduling
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t side_stream = nullptr;  // second lane of the resident kernel
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side_stream[2] = {nullptr, nullptr};  // lanes 1 and 2 of the resident kernel
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   int64_t steps_done = 0;
   int64_t phase = 0;  // steps since the last guard
   int64_t launches = 0;
@@ -152,15 +156,20 @@ bool valid_opts(const lb_ks_opts& o, std::string* why) {
     *why = "opts.threads_per_block must be 0 or a multiple of 32 in [32, 512]"; return false;
   }
   if (o.kernel == LB_KS_KERNEL_PLAIN && o.precision == LB_KS_F16S) { *why = "the plain kernel stores F64 or F32"; return false; }
+  if (o.cluster_size < 0 || o.cluster_size > 2) { *why = "opts.cluster_size must be 0, 1 or 2"; return false; }
   return true;
 }
 
 // ---------------------------------------------------------------- planning
 
-// Pieces of every run for (S, NT): rings (whole lattices) and segments (for lattices
-// longer than one block holds, with c_max * kseg halo sites per side); false if
-// some run cannot be held.
-bool plan_pieces(const lb_ks* h, int S, int NT, int kseg, std::vector<Piece>* rings, std::vector<Piece>* segs) {
+bool has_pair_lattices(const lb_ks* h, int S, int NT);
+
+// Pieces of every run for (S, NT): rings (whole lattices held by at most ring_cap
+// threads: NT, or 2 NT for two-block clusters) and segments (for longer lattices,
+// held by one block each, with c_max * kseg halo sites per side); false if some
+// run cannot be held.
+bool plan_pieces(const lb_ks* h, int S, int NT, int ring_cap, int kseg, std::vector<Piece>* rings,
+                 std::vector<Piece>* segs) {
   rings->clear();
   segs->clear();
   const int C = h->cmax;
@@ -174,7 +183,7 @@ bool plan_pieces(const lb_ks* h, int S, int NT, int kseg, std::vector<Piece>* ri
     for (int64_t m = 1;; ++m) {
       const int64_t n = m * N;
       const int64_t V = (n + S - 1) / S;
-      if (V > NT) break;
+      if (V > ring_cap) break;
       if (n > V * (S - 1)) {
         Piece p{};
         p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n; p.x0 = 0; p.st_lo = 0; p.st_hi = (int)N;
@@ -205,32 +214,65 @@ bool plan_pieces(const lb_ks* h, int S, int NT, int kseg, std::vector<Piece>* ri
   return true;
 }
 
-// First-fit decreasing packing of pieces into blocks of NT threads; bundles in
-// decreasing order of occupied threads (longest first).
-void pack_bundles(std::vector<Piece>& pieces, int NT, std::vector<Piece>* ordered, std::vector<int2>* bundles) {
+// Work groups of one lane during packing: first fit of pieces (threads nthr) into
+// groups of `cap` threads.
+struct Bins {
+  int cap = 0;
+  std::vector<std::vector<int>> members;
+  std::vector<int> used;
+
+  bool first_fit(std::vector<Piece>& pieces, int i) {
+    for (size_t b = 0; b < used.size(); ++b)
+      if (used[b] + pieces[i].nthr <= cap) {
+        pieces[i].t0 = used[b];
+        used[b] += pieces[i].nthr;
+        members[b].push_back(i);
+        return true;
+      }
+    return false;
+  }
+  void open(std::vector<Piece>& pieces, int i) {
+    pieces[i].t0 = 0;
+    members.push_back({i});
+    used.push_back(pieces[i].nthr);
+  }
+  // bundles in decreasing order of occupied threads (longest first)
+  void emit(const std::vector<Piece>& pieces, std::vector<Piece>* ordered, std::vector<int2>* bundles) const {
+    std::vector<int> order(members.size());
+    for (size_t b = 0; b < members.size(); ++b) order[b] = (int)b;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return used[a] > used[b]; });
+    ordered->clear();
+    bundles->clear();
+    for (int b : order) {
+      bundles->push_back(make_int2((int)ordered->size(), (int)members[b].size()));
+      for (int i : members[b]) ordered->push_back(pieces[i]);
+    }
+  }
+};
+
+std::vector<int> by_threads_desc(const std::vector<Piece>& pieces) {
   std::vector<int> idx(pieces.size());
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return pieces[a].nthr > pieces[b].nthr; });
-  std::vector<std::vector<int>> bins;
-  std::vector<int> used;
-  for (int i : idx) {
-    size_t b = 0;
-    for (; b < bins.size(); ++b)
-      if (used[b] + pieces[i].nthr <= NT) break;
-    if (b == bins.size()) { bins.emplace_back(); used.push_back(0); }
-    pieces[i].t0 = used[b];
-    used[b] += pieces[i].nthr;
-    bins[b].push_back(i);
+  return idx;
+}
+
+// First-fit decreasing packing of whole lattices: those longer than one block (more
+// than NT threads) each open a cluster pair (2 NT threads); the others fill the pairs'
+// spare threads first, then blocks of NT threads.
+void pack_rings(std::vector<Piece>& pieces, int NT, Bins* blocks, Bins* pairs) {
+  blocks->cap = NT;
+  pairs->cap = 2 * NT;
+  for (int i : by_threads_desc(pieces)) {
+    if (pieces[i].nthr > NT) pairs->open(pieces, i);
+    else if (!pairs->first_fit(pieces, i) && !blocks->first_fit(pieces, i)) blocks->open(pieces, i);
   }
-  std::vector<int> order(bins.size());
-  for (size_t b = 0; b < bins.size(); ++b) order[b] = (int)b;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return used[a] > used[b]; });
-  ordered->clear();
-  bundles->clear();
-  for (int b : order) {
-    bundles->push_back(make_int2((int)ordered->size(), (int)bins[b].size()));
-    for (int i : bins[b]) ordered->push_back(pieces[i]);
-  }
+}
+
+void pack_blocks(std::vector<Piece>& pieces, int NT, Bins* blocks) {
+  blocks->cap = NT;
+  for (int i : by_threads_desc(pieces))
+    if (!blocks->first_fit(pieces, i)) blocks->open(pieces, i);
 }
 
 int default_threads(int prec, int S) {
@@ -238,10 +280,14 @@ int default_threads(int prec, int S) {
   return S <= 8 ? 512 : (S <= 12 ? 384 : 256);
 }
 
-int upload_lane(lb_ks* h, Lane* L, std::vector<Piece>& pieces, int NT, int k) {
+int upload_lane(lb_ks* h, Lane* L, const std::vector<Piece>& pieces, const Bins& bins, int cl, int k, bool segmented,
+                double weight) {
   std::vector<Piece> ordered;
   std::vector<int2> bundles;
-  pack_bundles(pieces, NT, &ordered, &bundles);
+  bins.emit(pieces, &ordered, &bundles);
+  L->cl = cl;
+  L->segmented = segmented;
+  L->weight = weight;
   int rc;
   if ((rc = dalloc(h, &L->d_pieces, ordered.size()))) return rc;
   if ((rc = dalloc(h, &L->d_bundles, bundles.size()))) return rc;
@@ -255,11 +301,15 @@ int upload_lane(lb_ks* h, Lane* L, std::vector<Piece>& pieces, int NT, int k) {
 
 // Resident kernel plan.  Whole lattices (rings) run k_ring steps per launch; lattices
 // cut into segments run k_seg-step launches (their halo grows with the steps per
-// launch).  When both kinds exist they run as two lanes on disjoint sets of blocks,
-// on two streams, sized so that both finish a chunk of steps at about the same time.
-// S_force / NT_force > 0 pin the tiling (autotuner trials); seg_weight is the relative
-// cost of a segment bundle against a ring bundle used to split the blocks between lanes.
-int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, double seg_weight = 1.25) {
+// launch).  Rings of up to NT S sites run in single-block work groups; with cl = 2,
+// rings of up to 2 NT S sites run whole in cluster pairs (with smaller rings filling
+// the pairs' spare threads) instead of being cut into segments.  The kinds present run
+// as concurrent lanes on disjoint sets of blocks, on their own streams, sized so that
+// all finish a chunk of steps at about the same time.  S_force / NT_force / cl_force
+// > 0 pin the tiling (autotuner trials); lane_weight is the cost of a pair or segment
+// bundle relative to a single-block ring bundle, used to split the blocks.
+int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, double lane_weight = 1.25,
+                   int cl_force = 0) {
   std::vector<int> cand;
   if (S_force) cand.push_back(S_force);
   else if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
@@ -274,41 +324,57 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
     int kseg = h->opts.steps_per_launch ? h->opts.steps_per_launch
                                         : std::max(1, (int)((int64_t)NT * S / (20 * h->cmax)));
     kseg = std::min(kseg, kring);
+    // default: cluster pairs when some lattice needs more than one block and fits two
+    int cl = cl_force ? cl_force : h->opts.cluster_size;
+    if (cl == 0) cl = has_pair_lattices(h, S, NT) ? 2 : 1;
     std::vector<Piece> rings, segs;
-    if (!plan_pieces(h, S, NT, kseg, &rings, &segs)) continue;
-    int bps = 0;
+    if (!plan_pieces(h, S, NT, cl * NT, kseg, &rings, &segs)) continue;
+    Bins blocks, pairs, segbins;
+    pack_rings(rings, NT, &blocks, &pairs);
+    pack_blocks(segs, NT, &segbins);
+    int bps = 0, max_clusters = 0;
     cudaError_t e = resident_prepare(h->Q, h->prec, S, NT, &bps);
     if (e != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+    if (!pairs.used.empty()) {
+      e = resident_cluster_prepare(h->Q, h->prec, S, NT, &max_clusters);
+      if (e != cudaSuccess || max_clusters < 1) { cudaGetLastError(); continue; }
+    }
     int dev = 0, sms = 0;
     LBKS_CUDA(h, cudaGetDevice(&dev), "cudaGetDevice");
     LBKS_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-    const int slots = bps * sms;
+    const int slots = bps * sms;  // resident blocks
     int rc;
     h->nlanes = 0;
-    if (!rings.empty()) {
-      if ((rc = upload_lane(h, &h->lanes[h->nlanes], rings, NT, kring))) return rc;
-      h->lanes[h->nlanes++].segmented = false;
+    if (!blocks.used.empty()) {
+      if ((rc = upload_lane(h, &h->lanes[h->nlanes++], rings, blocks, 1, kring, false, 1.0))) return rc;
     }
-    if (!segs.empty()) {
-      if ((rc = upload_lane(h, &h->lanes[h->nlanes], segs, NT, kseg))) return rc;
-      h->lanes[h->nlanes++].segmented = true;
+    if (!pairs.used.empty()) {
+      if ((rc = upload_lane(h, &h->lanes[h->nlanes++], rings, pairs, 2, kring, false, lane_weight))) return rc;
     }
-    if (h->nlanes == 1) {
-      h->lanes[0].grid = std::min(h->lanes[0].nbundles, slots);
-    } else {
-      // Split the blocks: ring bundles take ceil(B1/G1) rounds of k_ring steps, segment
-      // bundles ceil(B2/G2) rounds of the same steps plus their launch-edge and halo
-      // overhead (weight seg_weight, default 1.25, chosen by the autotuner if enabled).
-      const int B1 = h->lanes[0].nbundles, B2 = h->lanes[1].nbundles;
-      int best = 1;
-      double bestT = 1e300;
-      for (int G1 = 1; G1 < slots; ++G1) {
-        const int G2 = slots - G1;
-        const double T = std::max<double>((B1 + G1 - 1) / G1, seg_weight * ((B2 + G2 - 1) / G2));
-        if (T < bestT) { bestT = T; best = G1; }
+    if (!segbins.used.empty()) {
+      if ((rc = upload_lane(h, &h->lanes[h->nlanes++], segs, segbins, 1, kseg, true, lane_weight))) return rc;
+    }
+    // Split the resident blocks between the lanes: lane l finishes a chunk of steps in
+    // about weight_l ceil(B_l / G_l) rounds of bundles on G_l work groups of cl_l blocks;
+    // work groups go one at a time to the lane that would finish last.
+    int used = 0;
+    for (int l = 0; l < h->nlanes; ++l) {
+      h->lanes[l].grid = 1;
+      used += h->lanes[l].cl;
+    }
+    for (;;) {
+      int worst = -1;
+      double worstT = -1.0;
+      for (int l = 0; l < h->nlanes; ++l) {
+        const Lane& L = h->lanes[l];
+        const double T = L.weight * ((L.nbundles + L.grid - 1) / L.grid);
+        if (T > worstT) { worstT = T; worst = l; }
       }
-      h->lanes[0].grid = std::min(B1, best);
-      h->lanes[1].grid = std::min(B2, slots - best);
+      Lane& W = h->lanes[worst];
+      const int cap = W.cl == 2 ? max_clusters : slots;
+      if (W.grid >= W.nbundles || W.grid >= cap || used + W.cl > slots) break;
+      ++W.grid;
+      used += W.cl;
     }
     h->S = S;
     h->NT = NT;
@@ -330,7 +396,7 @@ int issue_lane(lb_ks* h, const Lane& L, int64_t k, int from, bool in_place, cuda
     const int dst = (in_place && kk == k && cur == from) ? cur : 1 - cur;
     LBKS_CUDA(h, cudaMemsetAsync(L.d_queue, 0, sizeof(int), s), "queue reset");
     ResidentLaunch RL{h->Q, h->prec, h->S, h->NT, arena(h, cur), arena(h, dst), h->d_runs,
-                      L.d_pieces, L.d_bundles, L.nbundles, L.d_queue, (int)kk, L.grid};
+                      L.d_pieces, L.d_bundles, L.nbundles, L.d_queue, (int)kk, L.grid, L.cl, h->d_flags};
     LBKS_CUDA(h, launch_resident(RL, s), "resident step");
     *nk += 1;
     cur = dst;
@@ -368,18 +434,28 @@ int issue_steps(lb_ks* h, int64_t n, cudaStream_t s, int64_t* nk) {
       if (h->nlanes == 1) {
         if ((rc = issue_lane(h, h->lanes[0], k, h->cur, false, s, nk, &to))) return rc;
       } else {
-        // segments on the side stream; rings on s, one launch, ending in the same arena
-        const int64_t mseg = (k + h->lanes[1].k - 1) / h->lanes[1].k;
+        // lane 0 on s, the others on their side streams.  Whole-lattice lanes make one
+        // launch, in place when the segment lane (if any) makes an even number of
+        // launches, so that all lanes end in the same arena.
+        int64_t mseg = 1;
+        for (int l = 0; l < h->nlanes; ++l)
+          if (h->lanes[l].segmented) mseg = (k + h->lanes[l].k - 1) / h->lanes[l].k;
+        const bool has_seg = h->lanes[h->nlanes - 1].segmented;
         LBKS_CUDA(h, cudaEventRecord(h->ev_fork, s), "fork");
-        LBKS_CUDA(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0), "fork wait");
-        int to_seg = h->cur;
-        if ((rc = issue_lane(h, h->lanes[1], k, h->cur, false, h->side_stream, nk, &to_seg))) return rc;
-        Lane ring = h->lanes[0];
-        ring.k = (int)k;
-        if ((rc = issue_lane(h, ring, k, h->cur, (mseg % 2) == 0, s, nk, &to))) return rc;
-        LBKS_CUDA(h, cudaEventRecord(h->ev_join, h->side_stream), "join");
-        LBKS_CUDA(h, cudaStreamWaitEvent(s, h->ev_join, 0), "join wait");
-        if (to != to_seg) return fail(h, LB_KS_ECUDA, "internal: lanes ended in different arenas");
+        int to_l[3] = {h->cur, h->cur, h->cur};
+        for (int l = 0; l < h->nlanes; ++l) {
+          cudaStream_t sl = l == 0 ? s : h->side_stream[l - 1];
+          if (l > 0) LBKS_CUDA(h, cudaStreamWaitEvent(sl, h->ev_fork, 0), "fork wait");
+          Lane L = h->lanes[l];
+          if (!L.segmented) L.k = (int)k;
+          if ((rc = issue_lane(h, L, k, h->cur, !L.segmented && has_seg && (mseg % 2) == 0, sl, nk, &to_l[l]))) return rc;
+          if (l > 0) LBKS_CUDA(h, cudaEventRecord(h->ev_join[l - 1], sl), "join");
+        }
+        for (int l = 1; l < h->nlanes; ++l) {
+          LBKS_CUDA(h, cudaStreamWaitEvent(s, h->ev_join[l - 1], 0), "join wait");
+          if (to_l[l] != to_l[0]) return fail(h, LB_KS_ECUDA, "internal: lanes ended in different arenas");
+        }
+        to = to_l[0];
       }
       h->cur = to;
     } else {
@@ -460,12 +536,20 @@ void release_lanes(lb_ks* h) {
   h->nlanes = 0;
 }
 
+// True if some lattice is longer than one block of NT threads x S sites holds but
+// fits a cluster pair.
+bool has_pair_lattices(const lb_ks* h, int S, int NT) {
+  for (int64_t N : h->N)
+    if (N > (int64_t)NT * S && N <= 2LL * NT * S) return true;
+  return false;
+}
+
 // Autotuner of the resident kernel: times a few tilings (sites per thread, threads per
-// block) and lane splits on this handle's own lattices for a short run, and keeps the
-// fastest.  Runs before the state is initialised, on the zeroed arenas (the kernel's
-// work does not depend on the values).
+// block), ring work-group sizes (one block or a cluster pair) and lane splits on this
+// handle's own lattices for a short run, and keeps the fastest.  Runs before the state
+// is initialised, on the zeroed arenas (the kernel's work does not depend on the values).
 int autotune_resident(lb_ks* h) {
-  struct Cand { int S, NT; double w; };
+  struct Cand { int S, NT; double w; int cl; };
   std::vector<Cand> cands;
   std::vector<std::pair<int, int>> tilings;
   if (h->opts.sites_per_thread) {
@@ -475,8 +559,15 @@ int autotune_resident(lb_ks* h) {
   } else {
     tilings = {{12, 384}, {16, 256}, {8, 512}};
   }
-  for (auto& tl : tilings)
-    for (double w : {1.0, 1.3, 1.7}) cands.push_back({tl.first, tl.second, w});
+  for (auto& tl : tilings) {
+    const int NT = tl.second ? tl.second : default_threads(h->prec, tl.first);
+    for (int cl : {2, 1}) {
+      if (h->opts.cluster_size && cl != h->opts.cluster_size) continue;
+      if (cl == 2 && !has_pair_lattices(h, tl.first, NT)) continue;  // same plan as cl = 1
+      for (double w : {1.0, 1.3, 1.7}) cands.push_back({tl.first, tl.second, w, cl});
+    }
+  }
+  if (cands.empty()) return LB_KS_OK;  // keep the plan made before tuning
   const int64_t trial = std::max(2 * h->kseg, 100);
   cudaEvent_t e0, e1;
   LBKS_CUDA(h, cudaEventCreate(&e0), "tuner event");
@@ -486,7 +577,7 @@ int autotune_resident(lb_ks* h) {
   int rc = LB_KS_OK;
   for (const Cand& c : cands) {
     release_lanes(h);
-    if (setup_resident(h, false, c.S, c.NT, c.w) != LB_KS_OK) { cudaGetLastError(); continue; }
+    if (setup_resident(h, false, c.S, c.NT, c.w, c.cl) != LB_KS_OK) { cudaGetLastError(); continue; }
     if (h->nlanes < 2 && c.w != 1.0) continue;  // the split weight only matters with two lanes
     int64_t nk = 0;
     for (int rep = 0; rep < 2 && rc == LB_KS_OK; ++rep) {  // first repetition warms up
@@ -506,8 +597,9 @@ int autotune_resident(lb_ks* h) {
   if (rc != LB_KS_OK) return rc;
   release_lanes(h);
   if (best_ms < 1e300) {
-    if ((rc = setup_resident(h, true, best.S, best.NT, best.w)) != LB_KS_OK) return rc;
+    if ((rc = setup_resident(h, true, best.S, best.NT, best.w, best.cl)) != LB_KS_OK) return rc;
     h->tuned_weight = best.w;
+    h->tuned_cl = best.cl;
   } else if ((rc = setup_resident(h, true)) != LB_KS_OK) {
     return rc;
   }
@@ -523,6 +615,10 @@ int autotune_resident(lb_ks* h) {
 int check_flags(lb_ks* h) {
   int flag = 0;
   LBKS_CUDA(h, cudaMemcpy(&flag, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+  if (flag & 2) {
+    h->sticky = LB_KS_ETIMEOUT;
+    return fail(h, LB_KS_ETIMEOUT, "a bounded wait between the two blocks of a resident cluster ran out");
+  }
   if (flag) {
     h->sticky = LB_KS_EUNSTABLE;
     return fail(h, LB_KS_EUNSTABLE, "non-finite FP64 mass at a guard step (the run went unstable)");
@@ -712,10 +808,11 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "create capture stream"));
   if (kern == LB_KS_KERNEL_RESIDENT) {
-    if ((ce = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess)
-      return bail(cuda_fail(h, ce, "create lane stream"));
+    for (int l = 0; l < 2 && ce == cudaSuccess; ++l)
+      if ((ce = cudaStreamCreateWithFlags(&h->side_stream[l], cudaStreamNonBlocking)) == cudaSuccess)
+        ce = cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "create lane stream"));
     if (o.autotune && (rc = autotune_resident(h)) != LB_KS_OK) return bail(rc);
   }
 
@@ -749,6 +846,7 @@ void lb_ks_default_opts(lb_ks_opts* o) {
   o->kernel = LB_KS_KERNEL_AUTO;
   o->use_graph = 1;
   o->stream = nullptr;
+  o->cluster_size = 0;
 }
 
 int lb_ks_init(lb_ks_t** h, int scheme, int64_t N, double L, double dt, double tau, const double* rho0,
@@ -893,13 +991,18 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
 
 int64_t lb_ks_steps_done(const lb_ks_t* h) { return h ? h->steps_done : -1; }
 
-int lb_ks_describe(const lb_ks_t* h, int* kernel, int* spt, int* tpb, int* spl, int32_t* nruns, int64_t* total) {
+int lb_ks_describe(const lb_ks_t* h, int* kernel, int* spt, int* tpb, int* spl, int* cl, int32_t* nruns,
+                   int64_t* total) {
   if (!h) return LB_KS_EINVAL;
   const bool res = h->kernel == LB_KS_KERNEL_RESIDENT;
   if (kernel) *kernel = h->kernel;
   if (spt) *spt = res ? h->S : 0;
   if (tpb) *tpb = res ? h->NT : 0;
   if (spl) *spl = res ? h->kmax : 0;
+  if (cl) {
+    *cl = res ? 1 : 0;
+    for (int l = 0; res && l < h->nlanes; ++l) *cl = std::max(*cl, h->lanes[l].cl);
+  }
   if (nruns) *nruns = h->nruns;
   if (total) *total = h->total_sites;
   return LB_KS_OK;
@@ -911,12 +1014,15 @@ void lb_ks_free(lb_ks_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
-  if (h->side_stream) cudaStreamSynchronize(h->side_stream);
+  for (cudaStream_t ss : h->side_stream)
+    if (ss) cudaStreamSynchronize(ss);
   for (void* p : h->allocations) cudaFree(p);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  for (int l = 0; l < 2; ++l) {
+    if (h->side_stream[l]) cudaStreamDestroy(h->side_stream[l]);
+    if (h->ev_join[l]) cudaEventDestroy(h->ev_join[l]);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
   cudaGetLastError();
   delete h;
 }

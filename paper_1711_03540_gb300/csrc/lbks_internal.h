@@ -91,10 +91,15 @@ struct ResidentLaunch {
   int nbundles;
   int* queue;           // work counter, zeroed before each launch
   int ksteps;
-  int grid;
+  int grid;    // work groups (blocks, or clusters of cl blocks)
+  int cl = 1;  // blocks per work group: 1, or 2 (a thread block cluster)
+  int* flags = nullptr;  // error flags (bit 2: a bounded wait between the blocks of a cluster ran out)
 };
 bool resident_supported(int Q, int storage, int S, int NT);
 cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm);
+// Clusters of two blocks: the largest number of clusters resident at once.
+cudaError_t resident_cluster_prepare(int Q, int storage, int S, int NT, int* max_clusters);
+cudaError_t launch_resident_cluster(const ResidentLaunch& L, cudaStream_t s);
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s);
 
 // Diagnostic micro-benchmark of the FMA pipes (flop/s), used by the benchmark
