@@ -33,6 +33,8 @@ if ROOT not in sys.path:
 LB_STEPS_PER_STEP = 1000
 GUARD_EVERY = 500
 FLOP_PER_SITE_UPDATE = {7: 39, 5: 27}  # folded step, FMA = 2 flops: 6Q - 3
+# tau = 1 collapse: per c = 1..c_max two adds, an fma, an add, a mul, two fmas, then one add (FMA = 2)
+COLLAPSE_FLOP_PER_SITE_UPDATE = {7: 31, 5: 21}
 SM_COUNT_NOMINAL = 152
 
 
@@ -46,7 +48,8 @@ def parse():
     p.add_argument("--nmax", type=int, default=8192, help="largest lattice of the ensemble (profiling variants)")
     p.add_argument("--workload", default="ensemble", choices=["ensemble", "long"],
                    help="ensemble: 4096 lattices (default); long: one lattice of 2^24 sites")
-    p.add_argument("--kernel", default="resident", choices=["resident", "stream", "plain"])
+    p.add_argument("--kernel", default="resident", choices=["resident", "stream", "plain", "collapse"],
+                   help="collapse: the tau = 1 rho-only step, on the ensemble at tau = 1")
     p.add_argument("--precision", default="f32", choices=["f32", "f16s", "f64"])
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
     p.add_argument("--no-autotune", action="store_true",
@@ -219,14 +222,18 @@ def main():
     stream = torch.cuda.Stream()
     if args.workload == "long":
         wl = workloads.long_lattice(seed=rank_seed(workloads.BASE_SEED, rank, 1))
+    elif args.kernel == "collapse":
+        wl = workloads.ensemble_tau1(nruns=args.nruns, nmax=args.nmax,
+                                     seed=rank_seed(workloads.BASE_SEED, rank, args.nruns))
     else:
         wl = workloads.ensemble(nruns=args.nruns, nmax=args.nmax,
                                 seed=rank_seed(workloads.BASE_SEED, rank, args.nruns))
     Q = wl.scheme
     prec = {"f32": lb.F32, "f16s": lb.F16S, "f64": lb.F64}[args.precision]
-    kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN}[args.kernel]
+    kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN,
+            "collapse": lb.KERNEL_COLLAPSE}[args.kernel]
     opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
-                                 autotune=int(kern == lb.KERNEL_RESIDENT and not args.no_autotune),
+                                 autotune=int(kern in (lb.KERNEL_RESIDENT, lb.KERNEL_COLLAPSE) and not args.no_autotune),
                                  cluster_size=args.cluster, stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
     desc = lb.lb_ks_describe(h)
@@ -265,14 +272,19 @@ def main():
     props = torch.cuda.get_device_properties(local)
     elem = {lb.F64: 8, lb.F32: 4, lb.F16S: 2}[prec]
     kname = {lb.KERNEL_RESIDENT: "resident_kernel", lb.KERNEL_STREAM: "stream_step_kernel",
-             lb.KERNEL_PLAIN: "plain_step_kernel"}[desc["kernel"]]
+             lb.KERNEL_PLAIN: "plain_step_kernel", lb.KERNEL_COLLAPSE: "collapse_step_kernel"}[desc["kernel"]]
+    collapse = desc["kernel"] == lb.KERNEL_COLLAPSE
+    if collapse and desc["sites_per_thread"]:
+        kname = "collapse_resident_kernel"
+    flop_su = (COLLAPSE_FLOP_PER_SITE_UPDATE if collapse else FLOP_PER_SITE_UPDATE)[Q]
+    planes = 1 if collapse else Q  # stored planes read and written per site-update
     kname += "<%d,%s%s>" % (Q, args.precision.upper(), ",%d" % desc["sites_per_thread"] if desc["sites_per_thread"] else "")
-    if desc["kernel"] == lb.KERNEL_RESIDENT or prec == lb.F64:
+    if desc["kernel"] == lb.KERNEL_RESIDENT or prec == lb.F64 or (collapse and desc["sites_per_thread"]):
         # Arithmetic-bound.  The resident kernel's two lanes (whole lattices: one launch per
         # 500 steps; segmented lattices: short launches on a second stream) overlap, so the
         # launches of one benchmark step are timed together: algorithmic flops of the step /
         # CUDA-event step time (the guard's few-percent share is charged to the kernel).
-        flops_per_step = FLOP_PER_SITE_UPDATE[Q] * sites * LB_STEPS_PER_STEP
+        flops_per_step = flop_su * sites * LB_STEPS_PER_STEP
         achieved = flops_per_step / (step_mean_ms * 1e-3) / 1e12
         if prec == lb.F64:
             peak, basis = 1.25, "nominal GB300 FP64 rate (1.25 TFLOP/s)"
@@ -281,19 +293,20 @@ def main():
             basis = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (derived)"
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": None, "kernel": kname, "peak_basis": basis,
-                    "algorithmic": f"{FLOP_PER_SITE_UPDATE[Q]} flop/site-update x {sites} sites x "
+                    "algorithmic": f"{flop_su} flop/site-update x {sites} sites x "
                                    f"{LB_STEPS_PER_STEP} steps per benchmark step",
                     "time_basis": "CUDA events around each benchmark step on the launching stream"}
     else:
-        # HBM-bound, one launch per LB step: per launch one read and one write of the Q planes.
+        # HBM-bound, one launch per LB step: per launch one read and one write of the
+        # stored planes (Q, or the collapse's one).
         peaks, src = measured_peaks()
-        bytes_per_launch = 2 * Q * elem * sites
+        bytes_per_launch = 2 * planes * elem * sites
         launch_s = step_mean_ms * 1e-3 / LB_STEPS_PER_STEP
         achieved = bytes_per_launch / launch_s / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname,
                     "peak_basis": f"hbm_gbs of MEASURED_PEAKS.json ({src})",
-                    "algorithmic": f"{2 * Q * elem} B/site-update x {sites} sites per launch",
+                    "algorithmic": f"{2 * planes * elem} B/site-update x {sites} sites per launch",
                     "time_basis": "CUDA-event benchmark-step time / launches per step (guard charged to the kernel)"}
     line = {"metric": "lattice-site updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

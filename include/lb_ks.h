@@ -78,6 +78,14 @@ extern "C" {
 #define LB_KS_KERNEL_PLAIN 1    /* one thread per site, one launch per step (F64, F32) */
 #define LB_KS_KERNEL_STREAM 2   /* HBM-streaming tiles, one launch per step (F32, F16S) */
 #define LB_KS_KERNEL_RESIDENT 3 /* register-resident, many steps per launch (F64, F32, F16S) */
+/* tau = 1 only (every run): at tau = 1 the BGK collision of Eq. LB_equation_ordinary
+ * sets f* = f^eq(rho), so rho alone is the state and the step is the stencil
+ * rho'(x) = sum_i f^eq_i(rho(x - c_i)), evaluated with the +c and -c speeds paired:
+ * rho + sum_c A_c [rho(x-c) + rho(x+c) - 2 rho] + B_c [rho(x-c)^2 - rho(x+c)^2].
+ * One stored plane (rho - rhobar) instead of Q; the same results as the other
+ * families up to rounding (not bitwise).  F64 or F32; periodic or reservoir ends.
+ * Never chosen by LB_KS_KERNEL_AUTO. */
+#define LB_KS_KERNEL_COLLAPSE 4
 
 /* Reading of Eq. delta_M. */
 #define LB_KS_DM_DERIVED 0 /* bracket (T2+1)/(2(T1+1)) - (T3+1)/(T2+1), as Eq. KS_trunc2 needs */
@@ -91,10 +99,12 @@ typedef struct lb_ks_opts {
     int32_t recentre_every;    /* R > 0: every R steps compute the FP64 mass of every run and add
                                   (M0 - M)/N to f_0 at each site; 0 = never (default for F64) */
     int32_t kernel;            /* LB_KS_KERNEL_* */
-    int32_t steps_per_launch;  /* resident kernel: steps kept on chip per launch; 0 = auto */
+    int32_t steps_per_launch;  /* resident kernel: steps kept on chip per launch; 0 = auto.  For
+                                  the tau = 1 collapse, 1 selects its streaming kernel */
     int32_t sites_per_thread;  /* resident kernel: register slots per thread (4,6,8,12,16 for
-                                  F32/F16S; 4,6,8 for F64); 0 = auto */
-    int32_t threads_per_block; /* resident kernel: 128, 256 or 512; 0 = auto */
+                                  F32/F16S; 4,6,8 for F64; the tau = 1 collapse: 8,16,32 for
+                                  F32, 8,16 for F64); 0 = auto */
+    int32_t threads_per_block; /* resident kernel: a multiple of 32 up to 512; 0 = auto */
     int32_t use_graph;         /* 1 (default): replay captured CUDA graphs for step sequences */
     int32_t autotune;          /* resident kernel: 1 = at init, time a few tilings (sites per thread,
                                   threads per block, split of the blocks between whole and
@@ -163,7 +173,8 @@ LB_KS_API int lb_ks_batch_init(lb_ks_t **h, int scheme, int32_t nruns, const int
  * from outside carry the boundary state and those streaming out are dropped.
  * rho0 (sum N[r] values, host or device) initialises the nodes; its two end
  * values are replaced by the boundary values.  These lattices run on the plain
- * kernel family (each node pulls plane i from node j - c_i); the guard's
+ * kernel family (each node pulls plane i from node j - c_i), or on the tau = 1
+ * collapse when opts->kernel is LB_KS_KERNEL_COLLAPSE; the guard's
  * re-centring is not allowed (mass flows through the ends: recentre_every must
  * be 0); lb_ks_rho and lb_ks_mass_energy cover the N[r] nodes.
  * Errors: as lb_ks_batch_init, plus LB_KS_EINVAL for NULL or non-finite
@@ -206,7 +217,8 @@ LB_KS_API int lb_ks_state_bytes(const lb_ks_t *h, size_t *bytes);
  * checkpoint gives bitwise the same result as running straight through.
  * Layout: a 64-byte header; nruns int64 lattice sizes; nruns records of run
  * constants; nruns FP64 reference masses; last, the populations: scheme
- * planes of `plane` elements in the storage precision (8, 4 or 2 bytes),
+ * planes of `plane` elements in the storage precision (8, 4 or 2 bytes)
+ * (one plane, rho - rhobar, for LB_KS_KERNEL_COLLAPSE: header word 5 is then 1),
  * plane = sum over runs of N rounded up to a multiple of 32, run r starting
  * at the sum of the rounded sizes of the runs before it.  Populations are
  * stored as f_0 - rhobar, f_1, ..., f_{Q-1} (divided by the run's scale for

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbks.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["lbks_api.cu", "lbks_kernels_plain.cu", "lbks_kernels_stream.cu", "lbks_kernels_resident.cu", "lbks_kernels_cluster.cu",
+SOURCES = ["lbks_api.cu", "lbks_kernels_plain.cu", "lbks_kernels_stream.cu", "lbks_kernels_resident.cu", "lbks_kernels_cluster.cu", "lbks_kernels_collapse.cu",
            "lbks_params.cpp", "lbks_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

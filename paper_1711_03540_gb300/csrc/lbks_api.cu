@@ -54,6 +54,8 @@ struct Lane {
 
 struct lb_ks {
   int Q = 0, prec = 0, kernel = 0, cmax = 0;
+  int nplanes = 0;         // stored planes: Q, or 1 for the tau = 1 collapse (rho - rhobar)
+  bool collapse_resident = false;  // tau = 1 collapse on its register-resident kernel (lanes below)
   bool reservoir = false;  // lattices with fixed-value ends instead of periodic ones
   lb_ks_opts opts{};
   int32_t nruns = 0;
@@ -146,11 +148,12 @@ bool valid_opts(const lb_ks_opts& o, std::string* why) {
   if (o.precision < LB_KS_F64 || o.precision > LB_KS_F16S) { *why = "opts.precision must be 0, 1 or 2"; return false; }
   if (o.dm_variant != LB_KS_DM_DERIVED && o.dm_variant != LB_KS_DM_PRINTED) { *why = "opts.dm_variant must be 0 or 1"; return false; }
   if (o.recentre_every < 0) { *why = "opts.recentre_every must be >= 0"; return false; }
-  if (o.kernel < LB_KS_KERNEL_AUTO || o.kernel > LB_KS_KERNEL_RESIDENT) { *why = "opts.kernel must be 0..3"; return false; }
+  if (o.kernel < LB_KS_KERNEL_AUTO || o.kernel > LB_KS_KERNEL_COLLAPSE) { *why = "opts.kernel must be 0..4"; return false; }
+  if (o.kernel == LB_KS_KERNEL_COLLAPSE && o.precision == LB_KS_F16S) { *why = "the tau = 1 collapse stores F64 or F32"; return false; }
   if (o.steps_per_launch < 0) { *why = "opts.steps_per_launch must be >= 0"; return false; }
   if (o.sites_per_thread != 0 && o.sites_per_thread != 4 && o.sites_per_thread != 6 && o.sites_per_thread != 8 &&
-      o.sites_per_thread != 12 && o.sites_per_thread != 16) {
-    *why = "opts.sites_per_thread must be 0, 4, 6, 8, 12 or 16"; return false;
+      o.sites_per_thread != 12 && o.sites_per_thread != 16 && o.sites_per_thread != 32) {
+    *why = "opts.sites_per_thread must be 0, 4, 6, 8, 12, 16 or 32"; return false;
   }
   if (o.threads_per_block != 0 && (o.threads_per_block < 32 || o.threads_per_block > 512 || o.threads_per_block % 32)) {
     *why = "opts.threads_per_block must be 0 or a multiple of 32 in [32, 512]"; return false;
@@ -310,16 +313,22 @@ int upload_lane(lb_ks* h, Lane* L, const std::vector<Piece>& pieces, const Bins&
 // bundle relative to a single-block ring bundle, used to split the blocks.
 int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, double lane_weight = 1.25,
                    int cl_force = 0) {
+  const bool col = h->nplanes == 1;  // the tau = 1 collapse's resident kernel
+  auto supported = [&](int S, int NT) {
+    return col ? collapse_resident_supported(h->Q, h->prec, S, NT) : resident_supported(h->Q, h->prec, S, NT);
+  };
   std::vector<int> cand;
   if (S_force) cand.push_back(S_force);
   else if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
+  else if (col) cand = h->prec == kF64 ? std::vector<int>{16, 8} : std::vector<int>{32, 16, 8};
   else if (h->prec == kF64) cand = {8, 6, 4};
   else cand = {12, 8, 16, 6, 4};
   const int R = h->opts.recentre_every;
   for (int S : cand) {
     const int NT = NT_force ? NT_force
-                            : (h->opts.threads_per_block ? h->opts.threads_per_block : default_threads(h->prec, S));
-    if (!resident_supported(h->Q, h->prec, S, NT)) continue;
+                            : (h->opts.threads_per_block ? h->opts.threads_per_block
+                                                         : (col ? 256 : default_threads(h->prec, S)));
+    if (!supported(S, NT)) continue;
     const int kring = h->opts.steps_per_launch ? h->opts.steps_per_launch : (R > 0 ? std::min(R, 1000) : 1000);
     int kseg = h->opts.steps_per_launch ? h->opts.steps_per_launch
                                         : std::max(1, (int)((int64_t)NT * S / (20 * h->cmax)));
@@ -327,13 +336,14 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
     // default: cluster pairs when some lattice needs more than one block and fits two
     int cl = cl_force ? cl_force : h->opts.cluster_size;
     if (cl == 0) cl = has_pair_lattices(h, S, NT) ? 2 : 1;
+    if (col) cl = 1;  // no cluster variant of the collapse
     std::vector<Piece> rings, segs;
     if (!plan_pieces(h, S, NT, cl * NT, kseg, &rings, &segs)) continue;
     Bins blocks, pairs, segbins;
     pack_rings(rings, NT, &blocks, &pairs);
     pack_blocks(segs, NT, &segbins);
     int bps = 0, max_clusters = 0;
-    cudaError_t e = resident_prepare(h->Q, h->prec, S, NT, &bps);
+    cudaError_t e = col ? collapse_resident_prepare(h->Q, h->prec, S, NT, &bps) : resident_prepare(h->Q, h->prec, S, NT, &bps);
     if (e != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
     if (!pairs.used.empty()) {
       e = resident_cluster_prepare(h->Q, h->prec, S, NT, &max_clusters);
@@ -396,7 +406,8 @@ int issue_lane(lb_ks* h, const Lane& L, int64_t k, int from, bool in_place, cuda
     const int dst = (in_place && kk == k && cur == from) ? cur : 1 - cur;
     LBKS_CUDA(h, cudaMemsetAsync(L.d_queue, 0, sizeof(int), s), "queue reset");
     ResidentLaunch RL{h->Q, h->prec, h->S, h->NT, arena(h, cur), arena(h, dst), h->d_runs,
-                      L.d_pieces, L.d_bundles, L.nbundles, L.d_queue, (int)kk, L.grid, L.cl, h->d_flags};
+                      L.d_pieces, L.d_bundles, L.nbundles, L.d_queue, (int)kk, L.grid, L.cl, h->d_flags,
+                      h->nplanes == 1};
     LBKS_CUDA(h, launch_resident(RL, s), "resident step");
     *nk += 1;
     cur = dst;
@@ -409,7 +420,7 @@ int issue_lane(lb_ks* h, const Lane& L, int64_t k, int from, bool in_place, cuda
 // ---------------------------------------------------------------- step scheduling
 
 int issue_guard(lb_ks* h, cudaStream_t s, bool recentre, int64_t* nk) {
-  LBKS_CUDA(h, launch_mass_partials(h->Q, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles,
+  LBKS_CUDA(h, launch_mass_partials(h->nplanes, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles,
                                     h->n_stream_tiles, h->d_partials, s), "mass partials");
   LBKS_CUDA(h, launch_mass_finalize(h->nruns, h->d_stream_tile_begin, h->d_partials, h->d_runs, h->d_mass0, h->d_mass,
                                     h->d_energy, recentre ? h->d_delta : nullptr, h->d_flags, s), "mass finalize");
@@ -427,7 +438,7 @@ int issue_steps(lb_ks* h, int64_t n, cudaStream_t s, int64_t* nk) {
   const int64_t R = h->opts.recentre_every;
   while (n > 0) {
     int64_t k = 1;
-    if (h->kernel == LB_KS_KERNEL_RESIDENT) {
+    if (h->kernel == LB_KS_KERNEL_RESIDENT || h->collapse_resident) {
       k = std::min<int64_t>(n, h->kmax);
       if (R > 0) k = std::min<int64_t>(k, R - h->phase);
       int to = h->cur, rc;
@@ -459,7 +470,10 @@ int issue_steps(lb_ks* h, int64_t n, cudaStream_t s, int64_t* nk) {
       }
       h->cur = to;
     } else {
-      if (h->reservoir) {
+      if (h->kernel == LB_KS_KERNEL_COLLAPSE) {
+        LBKS_CUDA(h, launch_collapse_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
+                                          h->d_stream_tiles, h->n_stream_tiles, s), "collapse step");
+      } else if (h->reservoir) {
         LBKS_CUDA(h, launch_reservoir_step(h->Q, h->prec, arena(h, h->cur), arena(h, 1 - h->cur), h->d_runs,
                                            h->d_plain_tiles, h->n_plain_tiles, 0, s), "reservoir step");
       } else if (h->kernel == LB_KS_KERNEL_STREAM) {
@@ -552,16 +566,21 @@ int autotune_resident(lb_ks* h) {
   struct Cand { int S, NT; double w; int cl; };
   std::vector<Cand> cands;
   std::vector<std::pair<int, int>> tilings;
+  const bool col = h->nplanes == 1;  // the tau = 1 collapse's resident kernel
   if (h->opts.sites_per_thread) {
     tilings.push_back({h->opts.sites_per_thread, h->opts.threads_per_block});
+  } else if (col) {
+    if (h->prec == kF64) tilings = {{16, 256}, {16, 512}, {8, 512}};
+    else tilings = {{32, 256}, {32, 512}, {16, 512}};
   } else if (h->prec == kF64) {
     tilings = {{8, 256}, {6, 256}, {4, 256}};
   } else {
     tilings = {{12, 384}, {16, 256}, {8, 512}};
   }
   for (auto& tl : tilings) {
-    const int NT = tl.second ? tl.second : default_threads(h->prec, tl.first);
+    const int NT = tl.second ? tl.second : (col ? 256 : default_threads(h->prec, tl.first));
     for (int cl : {2, 1}) {
+      if (col && cl == 2) continue;
       if (h->opts.cluster_size && cl != h->opts.cluster_size) continue;
       if (cl == 2 && !has_pair_lattices(h, tl.first, NT)) continue;  // same plan as cl = 1
       for (double w : {1.0, 1.3, 1.7}) cands.push_back({tl.first, tl.second, w, cl});
@@ -658,6 +677,8 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     if (!(L[r] > 0.0) || !std::isfinite(L[r])) return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": L must be > 0");
     if (!(dt[r] > 0.0) || !std::isfinite(dt[r])) return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": dt must be > 0");
     if (!(tau[r] >= 1.0) || !std::isfinite(tau[r])) return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": tau must be >= 1");
+    if (o.kernel == LB_KS_KERNEL_COLLAPSE && tau[r] != 1.0)
+      return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": the collapse kernel needs tau = 1");
     total += N[r];
   }
   int ndev = 0;
@@ -676,6 +697,7 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   };
   h->Q = scheme;
   h->cmax = cmax;
+  h->nplanes = o.kernel == LB_KS_KERNEL_COLLAPSE ? 1 : scheme;
   h->prec = o.precision;
   h->opts = o;
   h->nruns = nruns;
@@ -762,7 +784,7 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   h->n_stream_tiles = (int)st.size();
 
   int rc;
-  const size_t fbytes = storage_bytes(h->prec) * (size_t)scheme * (size_t)h->plane;
+  const size_t fbytes = storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane;
   for (int b = 0; b < 2; ++b) {
     unsigned char* p = nullptr;
     if ((rc = dalloc(h, &p, fbytes))) return bail(rc);
@@ -795,7 +817,16 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   // Kernel family.
   int kern = o.kernel;
   h->reservoir = reservoir;
-  if (reservoir) {
+  if (kern == LB_KS_KERNEL_COLLAPSE) {
+    if (collapse_tile_sites() != TS) return bail(fail(h, LB_KS_ECUDA, "internal: collapse and streaming tiles differ"));
+    // periodic lattices: the register-resident collapse (many steps per launch), unless
+    // one step per launch is asked for; reservoir ends: the streaming collapse
+    if (!reservoir && o.steps_per_launch != 1) {
+      rc = setup_resident(h, false);
+      if (rc < 0) return bail(rc);
+      h->collapse_resident = rc == 0;
+    }
+  } else if (reservoir) {
     kern = LB_KS_KERNEL_PLAIN;
   } else if (kern == LB_KS_KERNEL_AUTO || kern == LB_KS_KERNEL_RESIDENT) {
     rc = setup_resident(h, kern == LB_KS_KERNEL_RESIDENT);
@@ -807,7 +838,7 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     return bail(cuda_fail(h, ce, "stream kernel setup"));
   if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "create capture stream"));
-  if (kern == LB_KS_KERNEL_RESIDENT) {
+  if (kern == LB_KS_KERNEL_RESIDENT || h->collapse_resident) {
     for (int l = 0; l < 2 && ce == cudaSuccess; ++l)
       if ((ce = cudaStreamCreateWithFlags(&h->side_stream[l], cudaStreamNonBlocking)) == cudaSuccess)
         ce = cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming);
@@ -816,17 +847,26 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     if (o.autotune && (rc = autotune_resident(h)) != LB_KS_OK) return bail(rc);
   }
 
-  // f = f^eq(rho0).
-  if ((ce = launch_init_eq(scheme, h->prec, arena(h, 0), h->d_runs, h->d_stream_tiles, h->n_stream_tiles, h->d_stage,
-                           h->d_rho_off, h->stream)) != cudaSuccess)
-    return bail(cuda_fail(h, ce, "init"));
-  h->launches += 1;
-  if (reservoir) {  // end nodes and ghosts at f^eq(rho_bc)
+  if (kern == LB_KS_KERNEL_COLLAPSE) {
+    // rho - rhobar in both arenas (reservoir ends and ghosts keep their values in both)
     for (int b = 0; b < 2; ++b)
-      if ((ce = launch_reservoir_step(scheme, h->prec, arena(h, b), arena(h, b), h->d_runs, h->d_plain_tiles,
-                                      h->n_plain_tiles, 1, h->stream)) != cudaSuccess)
-        return bail(cuda_fail(h, ce, "reservoir init"));
+      if ((ce = launch_collapse_init(h->prec, arena(h, b), h->d_runs, h->d_plain_tiles, h->n_plain_tiles, h->d_stage,
+                                     h->d_rho_off, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(h, ce, "init"));
     h->launches += 2;
+  } else {
+    // f = f^eq(rho0)
+    if ((ce = launch_init_eq(scheme, h->prec, arena(h, 0), h->d_runs, h->d_stream_tiles, h->n_stream_tiles, h->d_stage,
+                             h->d_rho_off, h->stream)) != cudaSuccess)
+      return bail(cuda_fail(h, ce, "init"));
+    h->launches += 1;
+    if (reservoir) {  // end nodes and ghosts at f^eq(rho_bc)
+      for (int b = 0; b < 2; ++b)
+        if ((ce = launch_reservoir_step(scheme, h->prec, arena(h, b), arena(h, b), h->d_runs, h->d_plain_tiles,
+                                        h->n_plain_tiles, 1, h->stream)) != cudaSuccess)
+          return bail(cuda_fail(h, ce, "reservoir init"));
+      h->launches += 2;
+    }
   }
   if ((ce = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, ce, "init sync"));
   *out = h;
@@ -874,7 +914,7 @@ int lb_ks_step(lb_ks_t* h, int64_t n) {
   if (h->sticky) return h->sticky;
   if (n < 0) return fail(h, LB_KS_EINVAL, "n must be >= 0");
   const int64_t R = h->opts.recentre_every;
-  const int64_t chunk_max = h->kernel == LB_KS_KERNEL_RESIDENT ? 64LL * h->kmax : 512;
+  const int64_t chunk_max = (h->kernel == LB_KS_KERNEL_RESIDENT || h->collapse_resident) ? 64LL * h->kmax : 512;
   while (n > 0) {
     int64_t c = std::min(n, chunk_max);
     if (R > 0) c = std::min<int64_t>(c, R - h->phase);
@@ -896,7 +936,7 @@ int lb_ks_rho(lb_ks_t* h, double* out) {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   if (h->sticky) return h->sticky;
   if (!out) return fail(h, LB_KS_EINVAL, "out must not be NULL");
-  LBKS_CUDA(h, launch_gather_rho(h->Q, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles, h->n_stream_tiles,
+  LBKS_CUDA(h, launch_gather_rho(h->nplanes, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles, h->n_stream_tiles,
                                  h->d_stage, h->d_rho_off, h->stream), "gather rho");
   h->launches += 1;
   LBKS_CUDA(h, cudaMemcpyAsync(out, h->d_stage, sizeof(double) * (size_t)h->total_sites, cudaMemcpyDefault, h->stream), "copy rho");
@@ -923,7 +963,7 @@ int lb_ks_mass_energy(lb_ks_t* h, double* mass, double* energy) {
 int lb_ks_state_bytes(const lb_ks_t* h, size_t* bytes) {
   if (!h || !bytes) return LB_KS_EINVAL;
   *bytes = 64 + sizeof(int64_t) * h->nruns + sizeof(RunDesc) * h->nruns + sizeof(double) * h->nruns +
-           storage_bytes(h->prec) * (size_t)h->Q * (size_t)h->plane;
+           storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane;
   return LB_KS_OK;
 }
 
@@ -935,7 +975,8 @@ int lb_ks_save(lb_ks_t* h, void* buf, size_t bytes) {
   if (!buf || bytes < need) return fail(h, LB_KS_EINVAL, "buffer too small for the checkpoint");
   unsigned char* p = static_cast<unsigned char*>(buf);
   std::memset(p, 0, 64);
-  uint32_t hdr[6] = {kMagic, kVersion, (uint32_t)h->Q, (uint32_t)h->prec, (uint32_t)h->nruns, 0};
+  uint32_t hdr[6] = {kMagic, kVersion, (uint32_t)h->Q, (uint32_t)h->prec, (uint32_t)h->nruns,
+                     h->nplanes == 1 ? 1u : 0u};
   std::memcpy(p, hdr, sizeof(hdr));
   int64_t hdr2[3] = {h->plane, h->steps_done, h->phase};
   std::memcpy(p + 24, hdr2, sizeof(hdr2));
@@ -946,7 +987,7 @@ int lb_ks_save(lb_ks_t* h, void* buf, size_t bytes) {
   p += sizeof(RunDesc) * h->nruns;
   std::memcpy(p, h->mass0_h.data(), sizeof(double) * h->nruns);
   p += sizeof(double) * h->nruns;
-  LBKS_CUDA(h, cudaMemcpyAsync(p, h->fbuf[h->cur], storage_bytes(h->prec) * (size_t)h->Q * (size_t)h->plane,
+  LBKS_CUDA(h, cudaMemcpyAsync(p, h->fbuf[h->cur], storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane,
                                cudaMemcpyDeviceToHost, h->stream), "save");
   LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   return check_flags(h);
@@ -963,7 +1004,7 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
   std::memcpy(hdr, p, sizeof(hdr));
   std::memcpy(hdr2, p + 24, sizeof(hdr2));
   if (hdr[0] != kMagic || hdr[1] != kVersion || hdr[2] != (uint32_t)h->Q || hdr[3] != (uint32_t)h->prec ||
-      hdr[4] != (uint32_t)h->nruns || hdr2[0] != h->plane)
+      hdr[4] != (uint32_t)h->nruns || hdr[5] != (h->nplanes == 1 ? 1u : 0u) || hdr2[0] != h->plane)
     return fail(h, LB_KS_EINVAL, "checkpoint does not match this handle (scheme, precision or runs)");
   p += 64;
   if (std::memcmp(p, h->N.data(), sizeof(int64_t) * h->nruns) != 0)
@@ -980,7 +1021,7 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
   h->mass0_h = m0;
   LBKS_CUDA(h, cudaMemcpy(h->d_runs, runs.data(), sizeof(RunDesc) * h->nruns, cudaMemcpyHostToDevice), "load runs");
   LBKS_CUDA(h, cudaMemcpy(h->d_mass0, m0.data(), sizeof(double) * h->nruns, cudaMemcpyHostToDevice), "load mass0");
-  LBKS_CUDA(h, cudaMemcpy(h->fbuf[h->cur], p, storage_bytes(h->prec) * (size_t)h->Q * (size_t)h->plane,
+  LBKS_CUDA(h, cudaMemcpy(h->fbuf[h->cur], p, storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane,
                           cudaMemcpyHostToDevice), "load populations");
   h->steps_done = hdr2[1];
   h->phase = hdr2[2];
@@ -994,7 +1035,7 @@ int64_t lb_ks_steps_done(const lb_ks_t* h) { return h ? h->steps_done : -1; }
 int lb_ks_describe(const lb_ks_t* h, int* kernel, int* spt, int* tpb, int* spl, int* cl, int32_t* nruns,
                    int64_t* total) {
   if (!h) return LB_KS_EINVAL;
-  const bool res = h->kernel == LB_KS_KERNEL_RESIDENT;
+  const bool res = h->kernel == LB_KS_KERNEL_RESIDENT || h->collapse_resident;
   if (kernel) *kernel = h->kernel;
   if (spt) *spt = res ? h->S : 0;
   if (tpb) *tpb = res ? h->NT : 0;

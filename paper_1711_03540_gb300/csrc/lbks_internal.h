@@ -94,9 +94,20 @@ struct ResidentLaunch {
   int grid;    // work groups (blocks, or clusters of cl blocks)
   int cl = 1;  // blocks per work group: 1, or 2 (a thread block cluster)
   int* flags = nullptr;  // error flags (bit 2: a bounded wait between the blocks of a cluster ran out)
+  bool collapse = false;  // the tau = 1 collapse (one stored plane) instead of the LB populations
 };
 bool resident_supported(int Q, int storage, int S, int NT);
 cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm);
+// The tau = 1 collapse (one stored plane).
+int collapse_tile_sites();
+cudaError_t launch_collapse_init(int storage, Arena dst, const RunDesc* runs, const Tile* tiles, int ntiles,
+                                 const double* rho0, const int64_t* rho_off, cudaStream_t s);
+cudaError_t launch_collapse_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
+                                 int ntiles, cudaStream_t s);
+bool collapse_resident_supported(int Q, int storage, int S, int NT);
+cudaError_t collapse_resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm);
+cudaError_t launch_collapse_resident(const ResidentLaunch& L, cudaStream_t s);
+
 // Clusters of two blocks: the largest number of clusters resident at once.
 cudaError_t resident_cluster_prepare(int Q, int storage, int S, int NT, int* max_clusters);
 cudaError_t launch_resident_cluster(const ResidentLaunch& L, cudaStream_t s);

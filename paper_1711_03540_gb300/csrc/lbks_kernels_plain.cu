@@ -311,9 +311,16 @@ cudaError_t launch_init_eq(int Q, int storage, Arena dst, const RunDesc* runs, c
   return cudaGetLastError();
 }
 
+// Q = 1: the single stored plane of the tau = 1 collapse (rho = rhobar + delta).
 cudaError_t launch_gather_rho(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles, int ntiles,
                               double* out, const int64_t* out_off, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
+  if (Q == 1) {
+    if (storage == kF64) gather_rho_kernel<1, kF64><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, out, out_off);
+    else if (storage == kF32) gather_rho_kernel<1, kF32><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, out, out_off);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
   LBKS_DISPATCH_Q_ST(Q, storage, (gather_rho_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, out, out_off)));
   return cudaGetLastError();
 }
@@ -337,6 +344,12 @@ cudaError_t launch_reservoir_step(int Q, int storage, Arena src, Arena dst, cons
 cudaError_t launch_mass_partials(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles, int ntiles,
                                  double* partials, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
+  if (Q == 1) {
+    if (storage == kF64) mass_partials_kernel<1, kF64><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, partials);
+    else if (storage == kF32) mass_partials_kernel<1, kF32><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, partials);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
   LBKS_DISPATCH_Q_ST(Q, storage, (mass_partials_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, partials)));
   return cudaGetLastError();
 }

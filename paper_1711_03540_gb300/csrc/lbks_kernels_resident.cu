@@ -40,6 +40,7 @@ cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_
 }
 
 cudaError_t launch_resident(const ResidentLaunch& L, cudaStream_t s) {
+  if (L.collapse) return launch_collapse_resident(L, s);
   const int Q = L.Q, storage = L.storage, S = L.S;
   if (!resident_supported(Q, storage, S, L.NT)) return cudaErrorInvalidValue;
   if (L.nbundles == 0 || L.grid == 0) return cudaSuccess;

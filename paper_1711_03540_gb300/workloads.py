@@ -10,7 +10,7 @@ identical inputs.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -99,6 +99,15 @@ def ensemble(nruns: int = 4096, nmin: int = 256, nmax: int = 8192, dx: float = 0
     N = np.array(Ns, dtype=np.int64)
     return Workload(f"d1q7_ensemble_{nruns}x[{nmin},{nmax}]", 7, N, N * dx, np.full(nruns, dt), np.array(taus),
                     np.concatenate(parts), steps)
+
+
+def ensemble_tau1(nruns: int = 4096, nmin: int = 256, nmax: int = 8192, dx: float = 0.2, dt: float = 5e-5,
+                  steps: int = 100_000, seed: int = BASE_SEED) -> Workload:
+    """The ensemble at tau = 1, the regime of the collapsed (rho-only) step:
+    dx = 0.2 and dt = 5e-5, below the critical time step of the Sec. 3 fit at
+    tau = 1 (7.2e-5 for D1Q7 at dx = 0.2).  Same lengths and modes as ensemble()."""
+    wl = ensemble(nruns, nmin, nmax, dx, dt, (1.0, 1.0), steps, seed)
+    return replace(wl, name=f"d1q7_ensemble_tau1_{nruns}x[{nmin},{nmax}]")
 
 
 def long_lattice(N: int = 1 << 24, dx: float = 0.1, dt: float = 1e-4, tau: float = 1.51, nmodes: int = 64,

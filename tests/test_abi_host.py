@@ -80,6 +80,7 @@ def test_tau_fit_matches_oracle_and_paper(lb):
     dict(scheme=6), dict(N=6), dict(L=0.0), dict(dt=-1e-4), dict(tau=0.95), dict(rho_nan=True),
     dict(opts=dict(precision=3)), dict(opts=dict(kernel=7)), dict(opts=dict(sites_per_thread=5)),
     dict(opts=dict(kernel=1, precision=2)), dict(opts=dict(threads_per_block=48)), dict(opts=dict(cluster_size=3)),
+    dict(opts=dict(kernel=4)), dict(opts=dict(kernel=4, precision=2)),
 ])
 def test_init_rejects_invalid_arguments(lb, bad):
     """Validation happens on the host before any device work: EINVAL on any
