@@ -173,8 +173,9 @@ LB_KS_API int lb_ks_batch_init(lb_ks_t **h, int scheme, int32_t nruns, const int
  * from outside carry the boundary state and those streaming out are dropped.
  * rho0 (sum N[r] values, host or device) initialises the nodes; its two end
  * values are replaced by the boundary values.  These lattices run on the plain
- * kernel family (each node pulls plane i from node j - c_i), or on the tau = 1
- * collapse when opts->kernel is LB_KS_KERNEL_COLLAPSE; the guard's
+ * kernel family (every node collides once and pushes plane i to node j + c_i when
+ * that node is interior), or on the tau = 1 collapse when opts->kernel is
+ * LB_KS_KERNEL_COLLAPSE; the guard's
  * re-centring is not allowed (mass flows through the ends: recentre_every must
  * be 0); lb_ks_rho and lb_ks_mass_energy cover the N[r] nodes.
  * Errors: as lb_ks_batch_init, plus LB_KS_EINVAL for NULL or non-finite

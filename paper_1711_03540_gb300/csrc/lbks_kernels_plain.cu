@@ -77,10 +77,12 @@ __global__ void __launch_bounds__(kPlainThreads) plain_step_kernel(Arena src, Ar
 }
 
 // Lattices with reservoir ends (the fixed end values of the front test, Table 5).
-// One thread per node j in [-c_max, N + c_max): reservoir nodes (j <= 0, j >= N-1,
-// ghosts included) are set to f^eq(rho_bc); an interior node pulls plane i from node
-// j - c_i, recomputing that node's collision with the same collide() as every other
-// kernel, so the values are those a push from j - c_i would deliver.
+// One thread per node j in [-c_max, N + c_max).  Reservoir nodes (j <= 0, j >= N-1,
+// ghosts included) rewrite their own populations as f^eq(rho_bc) in the
+// destination; every node collides its source populations once (a reservoir node
+// the f^eq(rho_bc) it holds) with the same collide() as every other kernel and
+// pushes plane i to j + c_i when that node is interior (pushes into reservoir
+// nodes are dropped), so each interior node receives exactly one value per plane.
 template <int Q, int ST>
 __global__ void __launch_bounds__(kPlainThreads) reservoir_step_kernel(Arena src, Arena dst,
                                                                        const RunDesc* __restrict__ runs,
@@ -100,19 +102,18 @@ __global__ void __launch_bounds__(kPlainThreads) reservoir_step_kernel(Arena src
       if (i == 0) v = __dsub_rn(v, d.rhobar);
       from_compute(static_cast<CT>(v), static_cast<CT>(d.inv_scale), fd + (int64_t)i * dst.plane + j);
     }
-    return;
   }
   if (reset_only) return;
   const T* fs = static_cast<const T*>(src.f) + d.off;
   const Coef<CT, Q> k = load_coef<CT, Q>(d);
+  CT g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) g[q] = to_compute(fs[(int64_t)q * src.plane + j], k.scale);
+  collide<Q, CT>(g, k);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const int64_t y = j - speed(i);
-    CT g[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) g[q] = to_compute(fs[(int64_t)q * src.plane + y], k.scale);
-    collide<Q, CT>(g, k);
-    from_compute(g[i], k.inv_scale, fd + (int64_t)i * dst.plane + j);
+    const int64_t y = j + speed(i);
+    if (y > 0 && y < d.N - 1) from_compute(g[i], k.inv_scale, fd + (int64_t)i * dst.plane + y);
   }
 }
 
