@@ -32,6 +32,12 @@ if ROOT not in sys.path:
 
 LB_STEPS_PER_STEP = 1000
 GUARD_EVERY = 500
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the resident kernel's
+# launches in one benchmark step, from one ncu capture of the full-size default workload
+# per plan (sites per thread, threads per block, blocks per whole-lattice work group).
+# A plan not listed, or a kernel changed since the capture, reports null.
+PROFILED_TRAFFIC = {("d1q7_ensemble_4096x[256,8192]", "f32", 16, 256, 2): 866.8e6,
+                    ("d1q7_ensemble_4096x[256,8192]", "f32", 12, 384, 2): 865.0e6}
 FLOP_PER_SITE_UPDATE = {7: 39, 5: 27}  # folded step, FMA = 2 flops: 6Q - 3
 # tau = 1 collapse: per c = 1..c_max two adds, an fma, an add, a mul, two fmas, then one add (FMA = 2)
 COLLAPSE_FLOP_PER_SITE_UPDATE = {7: 31, 5: 21}
@@ -56,6 +62,8 @@ def parse():
                    help="fixed default tiling (deterministic launch sequence, for profiling)")
     p.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
                    help="resident work group for whole lattices: 1 block, a 2-block cluster, 0 = auto")
+    p.add_argument("--spt", type=int, default=0, help="resident sites per thread (0 = auto; for profiling a plan)")
+    p.add_argument("--tpb", type=int, default=0, help="resident threads per block (0 = auto)")
     return p.parse_args()
 
 
@@ -234,7 +242,8 @@ def main():
             "collapse": lb.KERNEL_COLLAPSE}[args.kernel]
     opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
                                  autotune=int(kern in (lb.KERNEL_RESIDENT, lb.KERNEL_COLLAPSE) and not args.no_autotune),
-                                 cluster_size=args.cluster, stream=stream)
+                                 cluster_size=args.cluster, sites_per_thread=args.spt, threads_per_block=args.tpb,
+                                 stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
     desc = lb.lb_ks_describe(h)
     sites = wl.sites
@@ -291,8 +300,11 @@ def main():
         else:
             peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12
             basis = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (derived)"
+        plan = (wl.name, args.precision, desc["sites_per_thread"], desc["threads_per_block"], desc["cluster_size"])
+        traffic = PROFILED_TRAFFIC.get(plan) if desc["kernel"] == lb.KERNEL_RESIDENT else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": kname, "peak_basis": basis,
+                    "traffic": traffic, "traffic_unit": "bytes per benchmark step (ncu, DRAM read + write)",
+                    "kernel": kname, "peak_basis": basis,
                     "algorithmic": f"{flop_su} flop/site-update x {sites} sites x "
                                    f"{LB_STEPS_PER_STEP} steps per benchmark step",
                     "time_basis": "CUDA events around each benchmark step on the launching stream"}

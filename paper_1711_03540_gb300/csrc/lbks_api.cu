@@ -583,11 +583,13 @@ int autotune_resident(lb_ks* h) {
       if (col && cl == 2) continue;
       if (h->opts.cluster_size && cl != h->opts.cluster_size) continue;
       if (cl == 2 && !has_pair_lattices(h, tl.first, NT)) continue;  // same plan as cl = 1
-      for (double w : {1.0, 1.3, 1.7}) cands.push_back({tl.first, tl.second, w, cl});
+      for (double w : {1.0, 1.25, 1.6}) cands.push_back({tl.first, tl.second, w, cl});
     }
   }
   if (cands.empty()) return LB_KS_OK;  // keep the plan made before tuning
-  const int64_t trial = std::max(2 * h->kseg, 100);
+  // one full whole-lattice launch per trial (500 steps, or fewer when the guard
+  // interval or steps_per_launch is shorter), so the launch edges weigh as in a run
+  const int64_t trial = std::max<int64_t>(2 * h->kseg, std::min<int64_t>(h->kmax, 500));
   cudaEvent_t e0, e1;
   LBKS_CUDA(h, cudaEventCreate(&e0), "tuner event");
   LBKS_CUDA(h, cudaEventCreate(&e1), "tuner event");
