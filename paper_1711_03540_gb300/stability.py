@@ -137,3 +137,59 @@ def stability_map(scheme: int, dxs, dts, taus, T: float = 1.0, max_steps: int = 
             out.append(MapPoint(scheme, dx, dt, n, t_end, tmin, max_stable_tau(taus, st), G,
                                 lb_ks_tau_fit(scheme, dx, dt), list(taus), st, gs))
     return out
+
+
+def equal_accuracy(points5, points7, plateau_slack: float = 1.1, flop_ratio: float = 39.0 / 27.0) -> list[dict]:
+    """Sec. 3's cost comparison at equal accuracy (its Table 6) from two maps of the
+    same spacings, both run to the same T.  Per Delta X: D1Q5's plateau error is the
+    smallest G over its Delta T grid; D1Q5 runs at the largest Delta T whose G is
+    within plateau_slack of it; D1Q7 runs at the largest Delta T whose G is at most
+    that D1Q5 error.  The cost ratio counts steps per unit time times the per-step
+    work (flop_ratio: 39 flop per site-update for D1Q7 against 27 for D1Q5)."""
+    out = []
+    for dx in sorted({p.dx for p in points5}):
+        p5 = [p for p in points5 if p.dx == dx and np.isfinite(p.G)]
+        p7 = [p for p in points7 if p.dx == dx and np.isfinite(p.G)]
+        if not p5 or not p7:
+            continue
+        g_plateau = min(p.G for p in p5)
+        a = max((p for p in p5 if p.G <= plateau_slack * g_plateau), key=lambda p: p.dt)
+        ok7 = [p for p in p7 if p.G <= a.G]
+        if not ok7:
+            out.append({"dx": dx, "d1q5_dt": a.dt, "d1q5_tau": a.tau_min, "G": a.G, "d1q7_dt": None})
+            continue
+        b = max(ok7, key=lambda p: p.dt)
+        out.append({"dx": dx, "G_d1q5": a.G, "d1q5_dt": a.dt, "d1q5_tau": a.tau_min, "G_d1q7": b.G, "d1q7_dt": b.dt,
+                    "d1q7_tau": b.tau_min, "step_ratio": b.dt / a.dt,
+                    "cost_ratio_d1q5_over_d1q7": (b.dt / a.dt) / flop_ratio})
+    return out
+
+
+def main() -> None:
+    """Run both schemes' maps to T = 1 on the paper's spacings and print the maps and
+    the equal-accuracy comparison as one JSON line."""
+    import argparse
+    import json
+    import time
+
+    from . import build
+
+    p = argparse.ArgumentParser(description="stability and accuracy map of the front test (Sec. 3)")
+    p.add_argument("--T", type=float, default=1.0)
+    args = p.parse_args()
+    build.build()
+    taus = np.round(np.arange(1.0, 4.0001, 0.05), 2)
+    dts = [1e-6, 2e-6, 5e-6, 1e-5, 2e-5, 5e-5, 1e-4, 2e-4, 5e-4, 1e-3]
+    dxs = (0.05, 0.1, 0.2)
+    maps, secs = {}, {}
+    for Q in (5, 7):
+        t0 = time.perf_counter()
+        maps[Q] = stability_map(Q, dxs, dts, taus, T=args.T, max_steps=10 ** 9)
+        secs[Q] = time.perf_counter() - t0
+    rows = [{"Q": Q, "dx": m.dx, "dt": m.dt, "steps": m.steps, "tau_min": m.tau_min, "tau_max": m.tau_max,
+             "tau_fit": m.tau_fit, "G": m.G} for Q in (5, 7) for m in maps[Q]]
+    print(json.dumps({"T": args.T, "seconds": secs, "map": rows, "equal_accuracy": equal_accuracy(maps[5], maps[7])}))
+
+
+if __name__ == "__main__":
+    main()

@@ -52,3 +52,15 @@ def test_is_stable():
     big = ex.copy()
     big[10] = 3.0 + 3.0 * np.max(np.abs(ex - 3.0))
     assert not st.is_stable(big, ex)
+
+
+def test_equal_accuracy_picks_plateau_and_matching_step():
+    def pt(Q, dt, G):
+        return st.MapPoint(Q, 0.1, dt, int(1 / dt), 1.0, 1.0, 4.0, G, 1.0)
+    # D1Q5: plateau 1e-4 below dt = 1e-5, growing above; D1Q7 reaches 1e-4 up to dt = 5e-5
+    p5 = [pt(5, 1e-6, 1.00e-4), pt(5, 1e-5, 1.05e-4), pt(5, 1e-4, 1e-3)]
+    p7 = [pt(7, 1e-6, 1e-6), pt(7, 1e-5, 2e-5), pt(7, 5e-5, 1.0e-4), pt(7, 1e-4, 3e-4)]
+    (r,) = st.equal_accuracy(p5, p7)
+    assert r["d1q5_dt"] == 1e-5 and r["d1q7_dt"] == 5e-5
+    assert r["step_ratio"] == pytest.approx(5.0)
+    assert r["cost_ratio_d1q5_over_d1q7"] == pytest.approx(5.0 * 27 / 39)
