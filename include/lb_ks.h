@@ -142,6 +142,20 @@ LB_KS_API int lb_ks_params(int scheme, double dx, double dt, double tau, int dm_
 LB_KS_API double lb_ks_tau_fit(int scheme, double dX, double dT);
 
 /*
+ * Linear stability of the scheme (no GPU needed): the largest growth rate per
+ * unit time, ln(max |lambda|) / dt over all Q eigenvalues lambda of the linearised
+ * step about the uniform state rho_bar, at phases kappa = pi k / nk, k = 1..nk
+ * (the amplification matrix of Eq. LB_equation_ordinary with f^eq linearised:
+ * diag(exp(-i kappa c_j)) ((1 - 1/tau) I + (1/tau) a 1^T), a_j = A_j + 2 B_j rho_bar).
+ * Sec. 3 does not define "stable"; this library calls a run linearly unstable when
+ * the rate exceeds 1.05 x 1/4, the largest growth rate of the KS equation itself.
+ * *growth receives the rate.  Errors: as lb_ks_params, and LB_KS_EINVAL for
+ * growth == NULL or nk < 1.
+ */
+LB_KS_API int lb_ks_max_growth(int scheme, double dx, double dt, double tau, int dm_variant, double rho_bar, int nk,
+                               double *growth);
+
+/*
  * Create a handle for one periodic lattice of N sites on [0, L):
  * alpha = L / N, beta = dt, relaxation time tau (>= 1; T4 + 1 vanishes near
  * 0.908 and the paper uses tau >= 1, Sec. 3), and initial density
@@ -149,7 +163,10 @@ LB_KS_API double lb_ks_tau_fit(int scheme, double dX, double dT);
  * equilibrium, f_i = f^eq_i(rho0).  opts may be NULL (defaults).
  * Errors: LB_KS_EINVAL (unknown scheme, N < 2 c_max + 1, L <= 0, dt <= 0,
  * tau < 1, non-finite rho0, bad opts), LB_KS_ENOMEM, LB_KS_ECUDA.  On error
- * *h is set to NULL.
+ * *h is set to NULL.  Not an error: when the linear check of lb_ks_max_growth
+ * (nk = 128, about rho = 0) finds the run unstable, the handle is created and
+ * lb_ks_last_error(h) starts with "warning:" (batch handles: checked when the
+ * batch has at most 64 distinct (L/N, dt, tau)).
  */
 LB_KS_API int lb_ks_init(lb_ks_t **h, int scheme, int64_t N, double L, double dt, double tau, const double *rho0,
                const lb_ks_opts *opts);

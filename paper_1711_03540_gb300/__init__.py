@@ -61,6 +61,7 @@ ABI_FUNCTIONS = {
     "lb_ks_default_opts": (None, [C.POINTER(LbKsOpts)]),
     "lb_ks_params": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, _PD, _PD, _PD]),
     "lb_ks_tau_fit": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+    "lb_ks_max_growth": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, _PD]),
     "lb_ks_init": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int64, C.c_double, C.c_double, C.c_double, _P,
                              C.POINTER(LbKsOpts)]),
     "lb_ks_batch_init": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int32, _P, _P, _P, _P, _P, C.POINTER(LbKsOpts)]),
@@ -150,6 +151,14 @@ def lb_ks_params(scheme: int, dx: float, dt: float, tau: float, dm_variant: int 
 
 def lb_ks_tau_fit(scheme: int, dX: float, dT: float) -> float:
     return float(_load().lb_ks_tau_fit(scheme, dX, dT))
+
+
+def lb_ks_max_growth(scheme: int, dx: float, dt: float, tau: float, dm_variant: int = DM_DERIVED,
+                     rho_bar: float = 0.0, nk: int = 256) -> float:
+    """Largest linear growth rate per unit time over all branches and nk phases."""
+    g = C.c_double(0.0)
+    _check(_load().lb_ks_max_growth(scheme, dx, dt, tau, dm_variant, rho_bar, nk, C.byref(g)))
+    return g.value
 
 
 def lb_ks_init(scheme: int, N: int, L: float, dt: float, tau: float, rho0, opts: LbKsOpts | None = None):

@@ -2,6 +2,7 @@
 // layout, work planning, step scheduling with CUDA-graph replay, guard,
 // checkpointing.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -647,6 +648,33 @@ int check_flags(lb_ks* h) {
   return LB_KS_OK;
 }
 
+// Linear stability check (lb_ks_max_growth, nk = 128, about rho = 0) of every distinct
+// (dx, dt, tau) when a batch has at most 64 of them; a run whose growth rate exceeds
+// 1.05 x 1/4 leaves a warning in last_error (the handle is still created).
+void warn_if_linearly_unstable(lb_ks* h, const double* L, const double* dt, const double* tau) {
+  std::vector<std::array<double, 3>> seen;
+  for (int32_t r = 0; r < h->nruns; ++r) {
+    const double dx = L[r] / (double)(h->reservoir ? h->N[r] - 1 : h->N[r]);
+    const std::array<double, 3> key{dx, dt[r], tau[r]};
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+    seen.push_back(key);
+    if (seen.size() > 64) return;
+  }
+  int bad = 0, first = -1;
+  double worst = 0.0;
+  for (int32_t r = 0; r < h->nruns; ++r) {
+    const double dx = L[r] / (double)(h->reservoir ? h->N[r] - 1 : h->N[r]);
+    double g = 0.0;
+    if (lb_ks_max_growth(h->Q, dx, dt[r], tau[r], h->opts.dm_variant, 0.0, 128, &g) != LB_KS_OK) continue;
+    if (g > 1.05 * 0.25) {
+      if (bad++ == 0) { first = r; worst = g; }
+    }
+  }
+  if (bad)
+    h->err = "warning: " + std::to_string(bad) + " run(s) linearly unstable (run " + std::to_string(first) +
+             ": growth rate " + std::to_string(worst) + " per unit time > 1.05 x 1/4)";
+}
+
 int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const double* L, const double* dt,
            const double* tau, const double* rho0, const lb_ks_opts* opts, const double* rho_left = nullptr,
            const double* rho_right = nullptr) {
@@ -871,6 +899,7 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     }
   }
   if ((ce = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, ce, "init sync"));
+  warn_if_linearly_unstable(h, L, dt, tau);
   *out = h;
   return LB_KS_OK;
 }

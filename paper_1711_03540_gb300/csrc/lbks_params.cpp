@@ -1,5 +1,7 @@
 // Host precompute of the scheme's constants (FP64): lb_ks_params and lb_ks_tau_fit.
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 
 #include "../../include/lb_ks.h"
@@ -64,4 +66,89 @@ extern "C" double lb_ks_tau_fit(int scheme, double dX, double dT) {
   const double Bc = scheme == LB_KS_D1Q5 ? -13.2 * dX + 6.56 : -12.5 * dX + 6.64;
   const double lg = std::log10(dT);
   return lg >= -Bc ? A * (lg + Bc) * (lg + Bc) + 1.0 : 1.0;
+}
+
+// ---------------------------------------------------------------- linear stability
+
+namespace {
+
+// Largest |lambda| of the linearised step's amplification matrix at phase kappa:
+// G = D (r I + w a 1^T), D = diag(exp(-i kappa c_j)), r = 1 - 1/tau, w = 1/tau,
+// a_j = d f^eq_j / d rho at the background state.  G is a diagonal matrix plus a
+// rank-one term, so its characteristic polynomial is
+//   p(lambda) = prod_j (lambda - r d_j) - sum_j u_j prod_{k != j} (lambda - r d_k),
+// u = w D a; its roots are found by the Weierstrass (Durand-Kerner) iteration.
+double max_abs_eigenvalue(int Q, const double* a, double tau, double kappa) {
+  using cd = std::complex<double>;
+  const double r = 1.0 - 1.0 / tau, w = 1.0 / tau;
+  cd d[7], u[7];
+  for (int j = 0; j < Q; ++j) {
+    const int c = j == 0 ? 0 : ((j & 1) ? (j + 1) / 2 : -(j / 2));
+    d[j] = std::polar(1.0, -kappa * c);
+    u[j] = w * d[j] * a[j];
+  }
+  // coefficients of p, highest power first: p = sum_k coef[k] lambda^(Q - k)
+  cd coef[8] = {};
+  cd prod_all[8] = {};
+  prod_all[0] = 1.0;
+  int deg = 0;
+  for (int j = 0; j < Q; ++j) {  // prod_j (lambda - r d_j)
+    for (int k = deg + 1; k >= 1; --k) prod_all[k] -= r * d[j] * prod_all[k - 1];
+    ++deg;
+  }
+  for (int k = 0; k <= Q; ++k) coef[k] = prod_all[k];
+  for (int j = 0; j < Q; ++j) {  // - u_j prod_{k != j} (lambda - r d_k), degree Q - 1
+    cd q[8] = {};
+    q[0] = 1.0;
+    int dg = 0;
+    for (int k = 0; k < Q; ++k) {
+      if (k == j) continue;
+      for (int m = dg + 1; m >= 1; --m) q[m] -= r * d[k] * q[m - 1];
+      ++dg;
+    }
+    for (int m = 0; m < Q; ++m) coef[m + 1] -= u[j] * q[m];
+  }
+  auto eval = [&](cd z) {
+    cd v = coef[0];
+    for (int k = 1; k <= Q; ++k) v = v * z + coef[k];
+    return v;
+  };
+  cd z[7];
+  const cd seed(0.4, 0.9);
+  for (int k = 0; k < Q; ++k) z[k] = std::pow(seed, k) * 1.2;
+  for (int it = 0; it < 500; ++it) {
+    double change = 0.0;
+    for (int k = 0; k < Q; ++k) {
+      cd den = 1.0;
+      for (int m = 0; m < Q; ++m)
+        if (m != k) den *= z[k] - z[m];
+      if (std::abs(den) == 0.0) den = 1e-300;
+      const cd step = eval(z[k]) / den;
+      z[k] -= step;
+      change = std::max(change, std::abs(step));
+    }
+    if (change < 1e-15) break;
+  }
+  double best = 0.0;
+  for (int k = 0; k < Q; ++k) best = std::max(best, std::abs(z[k]));
+  return best;
+}
+
+}  // namespace
+
+extern "C" int lb_ks_max_growth(int scheme, double dx, double dt, double tau, int dm_variant, double rho_bar, int nk,
+                                double* growth) {
+  if (!growth || nk < 1) return LB_KS_EINVAL;
+  double A[7], B[7];
+  const int rc = lb_ks_params(scheme, dx, dt, tau, dm_variant, A, B, nullptr);
+  if (rc != LB_KS_OK) return rc;
+  double a[7];
+  for (int j = 0; j < scheme; ++j) a[j] = A[j] + 2.0 * B[j] * rho_bar;
+  double best = -HUGE_VAL;
+  for (int k = 1; k <= nk; ++k) {
+    const double kappa = M_PI * k / nk;
+    best = std::max(best, std::log(max_abs_eigenvalue(scheme, a, tau, kappa)) / dt);
+  }
+  *growth = best;
+  return LB_KS_OK;
 }

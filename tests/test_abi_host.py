@@ -116,3 +116,27 @@ def test_no_device_is_an_error_not_a_fallback(lb):
     with pytest.raises(lb.LbKsError) as e:
         lb.lb_ks_init(7, 64, 6.4, 1e-4, 1.5, np.zeros(64))
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("Q", [5, 7])
+@pytest.mark.parametrize("dx,dt,tau,rb", [(0.1, 1e-4, 1.5, 0.0), (0.1, 1e-4, 1.0, 0.0), (0.2, 5e-5, 1.0, 0.3),
+                                          (0.05, 1e-5, 2.0, -0.5), (0.0245, 5e-6, 3.0, 0.0), (0.4, 1e-3, 1.2, 1.0)])
+def test_max_growth_matches_oracle(lb, Q, dx, dt, tau, rb):
+    """The library's characteristic-polynomial eigenvalues against the oracle's
+    dense eigenvalue solver of the same amplification matrix."""
+    from oracle import analysis
+
+    g = lb.lb_ks_max_growth(Q, dx, dt, tau, rho_bar=rb, nk=64)
+    ref = analysis.max_growth(Q, dx, dt, tau, rho_bars=(rb,), nk=64)
+    assert g == pytest.approx(ref, rel=1e-6, abs=1e-6)
+
+
+def test_max_growth_classifies_as_the_oracle_around_the_critical_step(lb):
+    from oracle import analysis
+
+    for Q, dx, tau in ((5, 0.1, 1.0), (7, 0.1, 1.0), (7, 0.2, 1.5)):
+        dtc = analysis.critical_dt(Q, dx, tau)
+        assert lb.lb_ks_max_growth(Q, dx, 0.9 * dtc, tau) <= 1.05 * 0.25
+        assert lb.lb_ks_max_growth(Q, dx, 1.1 * dtc, tau) > 1.05 * 0.25
+    with pytest.raises(lb.LbKsError):
+        lb.lb_ks_max_growth(7, 0.1, 1e-4, 1.5, nk=0)

@@ -297,3 +297,19 @@ def test_unstable_run_is_reported_and_sticky(lb):
         assert e.value.code == -4
     finally:
         lb.lb_ks_free(h)
+
+
+def test_init_warns_about_linearly_unstable_runs(lb):
+    """The handle is created either way; last_error starts with "warning:" when the
+    linear check flags a run (D1Q7, dx = 0.1, dt = 1e-4 needs tau above ~1.5)."""
+    r0 = two_harmonic(64, 6.4)
+    h = lb.lb_ks_init(7, 64, 6.4, 1e-4, 1.0, r0)
+    try:
+        assert lb.lb_ks_last_error(h).startswith("warning:")
+    finally:
+        lb.lb_ks_free(h)
+    h = lb.lb_ks_init(7, 64, 6.4, 1e-4, 1.6, r0)
+    try:
+        assert lb.lb_ks_last_error(h) == "no error"
+    finally:
+        lb.lb_ks_free(h)
