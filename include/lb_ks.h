@@ -90,12 +90,21 @@ extern "C" {
 /* Reading of Eq. delta_M. */
 #define LB_KS_DM_DERIVED 0 /* bracket (T2+1)/(2(T1+1)) - (T3+1)/(T2+1), as Eq. KS_trunc2 needs */
 #define LB_KS_DM_PRINTED 1 /* bracket with (T3+1)/(T4+1) as printed */
+/* Flag, combinable with either reading (D1Q7 only): an ablation of the weight
+ * reading.  By default D1Q7 uses the D1Q5 sets w1, w2, w4 padded with zeros at
+ * c = +-3 (Sec. 2.3), the choice for which delta f^eq cancels the alpha^2 d6 error
+ * term; with this flag it uses w1, w2, w4 of the full 7-speed inverse of Appendix A's
+ * moment matrix (Eq. cond_weight for p = 0..6), whose 6th moments vanish, so that
+ * delta f^eq leaves the alpha^2 d6 term at its D1Q5 size with the opposite sign
+ * instead of removing it.  A negative control, not a usable scheme. */
+#define LB_KS_WEIGHTS_FULL_INVERSE 2
 
 typedef struct lb_ks lb_ks_t; /* opaque handle */
 
 typedef struct lb_ks_opts {
     int32_t precision;         /* LB_KS_F64 (default), LB_KS_F32, LB_KS_F16S */
-    int32_t dm_variant;        /* LB_KS_DM_DERIVED (default) or LB_KS_DM_PRINTED */
+    int32_t dm_variant;        /* LB_KS_DM_DERIVED (default) or LB_KS_DM_PRINTED, optionally
+                                  | LB_KS_WEIGHTS_FULL_INVERSE */
     int32_t recentre_every;    /* R > 0: every R steps compute the FP64 mass of every run and add
                                   (M0 - M)/N to f_0 at each site; 0 = never (default for F64) */
     int32_t kernel;            /* LB_KS_KERNEL_* */

@@ -20,6 +20,7 @@ _lib = None
 
 D1Q5, D1Q7 = 5, 7
 DM_DERIVED, DM_PRINTED = 0, 1
+WEIGHTS_FULL_INVERSE = 2  # flag (D1Q7): w1, w2, w4 of the full 7-speed inverse, an ablation
 
 
 def build(force: bool = False) -> str:
@@ -45,6 +46,7 @@ def load():
             pd = C.POINTER(C.c_double)
             lib.lbo_coefficients.argtypes = [i32, d, d, d, i32, pd]
             lib.lbo_weight.argtypes = [i32, i32, i32, pd]
+            lib.lbo_weight_full.argtypes = [i32, i32, pd]
             lib.lbo_speed.argtypes = [i32, i32]
             lib.lbo_feq.argtypes = [i32, d, d, d, i32, i32, d, pd]
             lib.lbo_run.argtypes = [i32, i64, d, d, d, i32, i32, i32, d, d, pd, i64, pd, pd]
@@ -73,6 +75,18 @@ def weight(Q: int, l: int) -> np.ndarray:
         if lib.lbo_weight(Q, l, i, C.byref(v)) != 0:
             raise ValueError(f"no weight w^({l}) for Q={Q}")
         out[i] = v.value
+    return out
+
+
+def weight_full(l: int) -> np.ndarray:
+    """w^(l)_i of the full 7-speed inverse of Appendix A's moment matrix."""
+    lib = load()
+    out = np.empty(7)
+    for i in range(7):
+        w = C.c_double()
+        if lib.lbo_weight_full(l, i, C.byref(w)) != 0:
+            raise ValueError("bad weight index")
+        out[i] = w.value
     return out
 
 

@@ -19,6 +19,8 @@
  *    dm_variant = 1 selects the printed (T4+1).
  *  - D1Q7 uses the D1Q5 weights w0, w1, w2, w4 padded with zeros at c = +-3,
  *    plus the 7-speed w6 of Eq. weight_D1Q7 (Sec. 2.3 points to both sets).
+ *    The dm_variant bit 2 (value 2) selects the other reading, w1, w2, w4 of the
+ *    full 7-speed inverse of Appendix A, as an ablation.
  *  - Velocity order is that of the Vandermonde columns of Appendix A:
  *    0, +1, -1, +2, -2, +3, -3.
  *  - "+-" in Eq. weight_D1Q5 is the value at +c, "-+" its negative.
@@ -52,6 +54,13 @@ static const double W4[7] = {1.0 / 4.0, -1.0 / 6.0, -1.0 / 6.0, 1.0 / 24.0, 1.0 
 /* Eq. weight_D1Q7 (7-speed set only). */
 static const double W5[7] = {0.0, 1.0 / 48.0, -1.0 / 48.0, -1.0 / 60.0, 1.0 / 60.0, 1.0 / 240.0, -1.0 / 240.0};
 static const double W6[7] = {-1.0 / 36.0, 1.0 / 48.0, 1.0 / 48.0, -1.0 / 120.0, -1.0 / 120.0, 1.0 / 720.0, 1.0 / 720.0};
+/* The other rows of the full inverse of Appendix A's 7x7 moment matrix (Eq.
+ * cond_weight for p = 0..6; the appendix prints only w5 and w6 of it), used only by
+ * the weight ablation (variant bit 2): the alternative reading of Sec. 2.3. */
+static const double WF1[7] = {0.0, 3.0 / 4.0, -3.0 / 4.0, -3.0 / 20.0, 3.0 / 20.0, 1.0 / 60.0, -1.0 / 60.0};
+static const double WF2[7] = {-49.0 / 36.0, 3.0 / 4.0, 3.0 / 4.0, -3.0 / 40.0, -3.0 / 40.0, 1.0 / 180.0, 1.0 / 180.0};
+static const double WF3[7] = {0.0, -13.0 / 48.0, 13.0 / 48.0, 1.0 / 6.0, -1.0 / 6.0, -1.0 / 48.0, 1.0 / 48.0};
+static const double WF4[7] = {7.0 / 18.0, -13.0 / 48.0, -13.0 / 48.0, 1.0 / 12.0, 1.0 / 12.0, -1.0 / 144.0, -1.0 / 144.0};
 
 /* Deliberate mistakes that the tests plant to show that the pins catch them.
  * 0 = none (the only value used outside those tests). */
@@ -74,6 +83,14 @@ int lbo_weight(int Q, int l, int i, double *w) {
     return LBO_OK;
 }
 
+/* w^(l)_i of the full 7-speed inverse (l = 0..6), for the weight ablation and its pins. */
+int lbo_weight_full(int l, int i, double *w) {
+    if (i < 0 || i >= 7 || l < 0 || l > 6) return LBO_EINVAL;
+    const double *tab[7] = {W0, WF1, WF2, WF3, WF4, W5, W6};
+    *w = tab[l][i];
+    return LBO_OK;
+}
+
 /* Eq. T_form: closed forms of T_i = sum_{n>=1} (1-1/tau)^n [(n+1)^i - n^i], tau > 1/2. */
 static void t_closed_forms(double tau, double T[5]) {
     T[0] = 0.0;
@@ -92,6 +109,7 @@ static void t_closed_forms(double tau, double T[5]) {
  */
 int lbo_coefficients(int Q, double alpha, double beta, double tau, int dm_variant, double out[9]) {
     if ((Q != 5 && Q != 7) || !(alpha > 0.0) || !(beta > 0.0) || !(tau > 0.5)) return LBO_EINVAL;
+    if (dm_variant < 0 || dm_variant > 3) return LBO_EINVAL;
     double T[5];
     t_closed_forms(tau, T);
     double J = beta / (2.0 * alpha);
@@ -99,7 +117,7 @@ int lbo_coefficients(int Q, double alpha, double beta, double tau, int dm_varian
     double M = -24.0 * beta * (T[1] + 1.0) / (pow(alpha, 4) * (T[4] + 1.0));
     double dM = 0.0, E = 0.0;
     if (Q == 7) {
-        double second = dm_variant == 1 ? (T[3] + 1.0) / (T[4] + 1.0) : (T[3] + 1.0) / (T[2] + 1.0);
+        double second = (dm_variant & 1) ? (T[3] + 1.0) / (T[4] + 1.0) : (T[3] + 1.0) / (T[2] + 1.0);
         dM = -24.0 * beta * beta * (T[1] + 1.0) / (pow(alpha, 4) * (T[4] + 1.0)) *
              ((T[2] + 1.0) / (2.0 * (T[1] + 1.0)) - second);
         E = 120.0 * (T[1] + 1.0) * beta / ((T[4] + 1.0) * pow(alpha, 4));
@@ -119,6 +137,7 @@ int lbo_coefficients(int Q, double alpha, double beta, double tau, int dm_varian
 /* Scheme constants held by one run. */
 typedef struct {
     int Q;
+    int full_weights; /* D1Q7 weight ablation: the full 7-speed inverse for w1, w2, w4 */
     double tau, J, K, M, dM, E;
 } scheme_t;
 
@@ -128,6 +147,7 @@ static int make_scheme(int Q, double alpha, double beta, double tau, int dm_vari
     int rc = lbo_coefficients(Q, alpha, beta, tau, dm_variant, c);
     if (rc) return rc;
     s->Q = Q;
+    s->full_weights = Q == 7 && (dm_variant & 2);
     s->tau = tau;
     s->J = advection ? c[4] : 0.0;
     s->K = c[5];
@@ -145,11 +165,14 @@ static int make_scheme(int Q, double alpha, double beta, double tau, int dm_vari
 static void equilibrium(const scheme_t *s, double rho, double *feq) {
     for (int i = 0; i < s->Q; ++i) {
         double lin;
+        const double *w1 = s->full_weights ? WF1 : W1;
+        const double *w2 = s->full_weights ? WF2 : W2;
+        const double *w4 = s->full_weights ? WF4 : W4;
         if (s->Q == 5)
-            lin = W0[i] + s->K * W2[i] + s->M * W4[i];
+            lin = W0[i] + s->K * w2[i] + s->M * w4[i];
         else
-            lin = W0[i] + s->K * W2[i] + (s->M + s->dM) * W4[i] + s->E * W6[i];
-        feq[i] = rho * lin + rho * rho * s->J * W1[i];
+            lin = W0[i] + s->K * w2[i] + (s->M + s->dM) * w4[i] + s->E * W6[i];
+        feq[i] = rho * lin + rho * rho * s->J * w1[i];
     }
 }
 

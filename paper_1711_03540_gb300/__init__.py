@@ -32,6 +32,7 @@ D1Q5, D1Q7 = 5, 7
 F64, F32, F16S = 0, 1, 2
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_STREAM, KERNEL_RESIDENT, KERNEL_COLLAPSE = 0, 1, 2, 3, 4
 DM_DERIVED, DM_PRINTED = 0, 1
+WEIGHTS_FULL_INVERSE = 2  # flag: D1Q7 with the full 7-speed inverse weights (an ablation)
 STATUS = {0: "LB_KS_OK", -1: "LB_KS_EINVAL", -2: "LB_KS_ENOMEM", -3: "LB_KS_ECUDA", -4: "LB_KS_EUNSTABLE",
           -5: "LB_KS_ETIMEOUT"}
 

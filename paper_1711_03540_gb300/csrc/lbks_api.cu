@@ -147,7 +147,9 @@ Arena arena(lb_ks* h, int which) { return Arena{h->fbuf[which], h->plane}; }
 
 bool valid_opts(const lb_ks_opts& o, std::string* why) {
   if (o.precision < LB_KS_F64 || o.precision > LB_KS_F16S) { *why = "opts.precision must be 0, 1 or 2"; return false; }
-  if (o.dm_variant != LB_KS_DM_DERIVED && o.dm_variant != LB_KS_DM_PRINTED) { *why = "opts.dm_variant must be 0 or 1"; return false; }
+  if (o.dm_variant < 0 || o.dm_variant > (LB_KS_DM_PRINTED | LB_KS_WEIGHTS_FULL_INVERSE)) {
+    *why = "opts.dm_variant must be 0..3 (LB_KS_DM_* | LB_KS_WEIGHTS_FULL_INVERSE)"; return false;
+  }
   if (o.recentre_every < 0) { *why = "opts.recentre_every must be >= 0"; return false; }
   if (o.kernel < LB_KS_KERNEL_AUTO || o.kernel > LB_KS_KERNEL_COLLAPSE) { *why = "opts.kernel must be 0..4"; return false; }
   if (o.kernel == LB_KS_KERNEL_COLLAPSE && o.precision == LB_KS_F16S) { *why = "the tau = 1 collapse stores F64 or F32"; return false; }

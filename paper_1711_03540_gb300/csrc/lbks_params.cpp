@@ -16,6 +16,12 @@ constexpr double kW1[7] = {0.0, 2.0 / 3.0, -2.0 / 3.0, -1.0 / 12.0, 1.0 / 12.0, 
 constexpr double kW2[7] = {-5.0 / 4.0, 2.0 / 3.0, 2.0 / 3.0, -1.0 / 24.0, -1.0 / 24.0, 0, 0};
 constexpr double kW4[7] = {1.0 / 4.0, -1.0 / 6.0, -1.0 / 6.0, 1.0 / 24.0, 1.0 / 24.0, 0, 0};
 constexpr double kW6[7] = {-1.0 / 36.0, 1.0 / 48.0, 1.0 / 48.0, -1.0 / 120.0, -1.0 / 120.0, 1.0 / 720.0, 1.0 / 720.0};
+// Ablation (LB_KS_WEIGHTS_FULL_INVERSE): w1, w2, w4 of the full 7-speed inverse of
+// Appendix A's D1Q7 moment matrix (the rule of Eq. cond_weight for p = 0..6; the
+// appendix prints only w5 and w6 of that inverse).
+constexpr double kF1[7] = {0.0, 3.0 / 4.0, -3.0 / 4.0, -3.0 / 20.0, 3.0 / 20.0, 1.0 / 60.0, -1.0 / 60.0};
+constexpr double kF2[7] = {-49.0 / 36.0, 3.0 / 4.0, 3.0 / 4.0, -3.0 / 40.0, -3.0 / 40.0, 1.0 / 180.0, 1.0 / 180.0};
+constexpr double kF4[7] = {7.0 / 18.0, -13.0 / 48.0, -13.0 / 48.0, 1.0 / 12.0, 1.0 / 12.0, -1.0 / 144.0, -1.0 / 144.0};
 
 }  // namespace
 
@@ -24,7 +30,7 @@ extern "C" int lb_ks_params(int scheme, double dx, double dt, double tau, int dm
   if (scheme != LB_KS_D1Q5 && scheme != LB_KS_D1Q7) return LB_KS_EINVAL;
   if (!(dx > 0.0) || !(dt > 0.0) || !(tau > 0.5) || !std::isfinite(dx) || !std::isfinite(dt) || !std::isfinite(tau))
     return LB_KS_EINVAL;
-  if (dm_variant != LB_KS_DM_DERIVED && dm_variant != LB_KS_DM_PRINTED) return LB_KS_EINVAL;
+  if (dm_variant < 0 || dm_variant > (LB_KS_DM_PRINTED | LB_KS_WEIGHTS_FULL_INVERSE)) return LB_KS_EINVAL;
   if (!A || !B) return LB_KS_EINVAL;
   const double alpha = dx, beta = dt;
   // Eq. T_form, as T_i + 1.
@@ -41,15 +47,19 @@ extern "C" int lb_ks_params(int scheme, double dx, double dt, double tau, int dm
   if (scheme == LB_KS_D1Q7) {
     // Eq. delta_M; the bracket's second term is (T3+1)/(T2+1) in the derived
     // reading (the one that cancels the beta d4 term of Eq. KS_trunc2).
-    const double second = dm_variant == LB_KS_DM_PRINTED ? t3 / t4 : t3 / t2;
+    const double second = (dm_variant & LB_KS_DM_PRINTED) ? t3 / t4 : t3 / t2;
     dM = -24.0 * beta * beta * t1 / (a4 * t4) * (t2 / (2.0 * t1) - second);
     // delta f^eq of Sec. 2.2: coefficient of rho w6.
     E = 120.0 * t1 * beta / (t4 * a4);
   }
   const double Mp = M + dM;
+  const bool full = scheme == LB_KS_D1Q7 && (dm_variant & LB_KS_WEIGHTS_FULL_INVERSE);
+  const double* w1 = full ? kF1 : kW1;
+  const double* w2 = full ? kF2 : kW2;
+  const double* w4 = full ? kF4 : kW4;
   for (int i = 0; i < scheme; ++i) {
-    A[i] = kW0[i] + K * kW2[i] + Mp * kW4[i] + E * kW6[i];
-    B[i] = J * kW1[i];
+    A[i] = kW0[i] + K * w2[i] + Mp * w4[i] + E * kW6[i];
+    B[i] = J * w1[i];
     if (!std::isfinite(A[i]) || !std::isfinite(B[i])) return LB_KS_EINVAL;
   }
   if (coef) {

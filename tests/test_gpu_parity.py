@@ -175,6 +175,19 @@ def test_printed_delta_m_variant_matches_oracle_and_differs(lb):
     assert np.max(np.abs(ref_p - ref_d)) > 1e-9 * np.abs(ref_d).max()
 
 
+def test_full_inverse_weight_ablation_matches_oracle(lb):
+    """The weight ablation (full 7-speed inverse for D1Q7's w1, w2, w4) runs on the
+    GPU with the oracle's same reading; it differs from the default reading."""
+    N, L, dt, tau, n = 400, 40.0, 1e-4, 2.0, 500
+    r0 = two_harmonic(N, L)
+    ref_f = ora.run(7, r0, L / N, dt, tau, n, dm_variant=ora.WEIGHTS_FULL_INVERSE)
+    ref_d = ora.run(7, r0, L / N, dt, tau, n)
+    for kern in (1, 3):
+        out, _ = run_gpu(lb, 7, N, L, dt, tau, r0, n, dm_variant=lb.WEIGHTS_FULL_INVERSE, kernel=kern)
+        assert np.max(np.abs(out - ref_f)) <= 1e-12 * np.abs(ref_f).max()
+    assert np.max(np.abs(ref_f - ref_d)) > 1e-9 * np.abs(ref_d).max()
+
+
 def test_zero_steps_returns_initial_density(lb):
     r0 = two_harmonic(100)
     for prec in (0, 1):

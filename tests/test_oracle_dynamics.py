@@ -129,3 +129,29 @@ def test_stability_ordering_at_dx_0p1():
     d7 = analysis.critical_dt(7, 0.1, 1.0, lo=1e-7, hi=1e-3, iters=18)
     assert d7 < d5
     assert d7 > 0.1 ** 4 / 90
+
+
+def test_full_inverse_weights_satisfy_the_moment_rule_and_give_the_printed_w5_w6():
+    """Appendix A: the full 7-speed inverse (Eq. cond_weight for p = 0..6); the paper
+    prints only its w5 and w6, which the oracle's D1Q7 set uses."""
+    c = lbks.speeds(7).astype(float)
+    for l in range(7):
+        w = lbks.weight_full(l)
+        for p in range(7):
+            assert abs((c ** p * w).sum() - (1.0 if p == l else 0.0)) < 1e-12
+    np.testing.assert_array_equal(lbks.weight_full(5), lbks.weight(7, 5))
+    np.testing.assert_array_equal(lbks.weight_full(6), lbks.weight(7, 6))
+
+
+@pytest.mark.parametrize("alpha,beta,tau", CASES)
+def test_full_inverse_weights_flip_the_alpha2_d6_error(alpha, beta, tau):
+    """The weight reading of Sec. 2.3 (a negative control): with the D1Q5 sets padded
+    with zeros at c = +-3, delta f^eq removes the alpha^2 d6 error of D1Q5; with the
+    full 7-speed inverse (whose 6th moments vanish) the same delta f^eq leaves that
+    error at D1Q5's size with the opposite sign."""
+    _, c6_5 = _fit_error_coefficients(5, alpha, beta, tau)
+    _, c6_pad = _fit_error_coefficients(7, alpha, beta, tau)
+    c4_full, c6_full = _fit_error_coefficients(7, alpha, beta, tau, lbks.WEIGHTS_FULL_INVERSE)
+    assert abs(c6_pad) < 0.02 * abs(c6_5)
+    assert c6_full == pytest.approx(-c6_5, rel=0.05)
+    assert abs(c4_full) < 1e-2 * beta  # delta M still removes the beta d4 term
