@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lb_ks.h"
@@ -602,7 +603,7 @@ int autotune_resident(lb_ks* h) {
   for (const Cand& c : cands) {
     release_lanes(h);
     if (setup_resident(h, false, c.S, c.NT, c.w, c.cl) != LB_KS_OK) { cudaGetLastError(); continue; }
-    if (h->nlanes < 2 && c.w != 1.0) continue;  // the split weight only matters with two lanes
+    if (h->nlanes < 2 && c.w != 1.0) continue;  // the split weight only matters with more than one lane
     int64_t nk = 0;
     for (int rep = 0; rep < 2 && rc == LB_KS_OK; ++rep) {  // first repetition warms up
       cudaEventRecord(e0, h->stream);
@@ -737,64 +738,111 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   h->N.assign(N, N + nruns);
   h->total_sites = total;
 
-  // Host copy of rho0 (host or device pointer): validation, mean, scale, mass.
-  std::vector<double> r0((size_t)total);
-  ce = cudaMemcpy(r0.data(), rho0, sizeof(double) * (size_t)total, cudaMemcpyDefault);
-  if (ce != cudaSuccess) { cudaGetLastError(); return bail(fail(h, LB_KS_EINVAL, std::string("cannot read rho0: ") + cudaGetErrorString(ce))); }
+  // rho0 is read in place when the host can read it; a device pointer is copied down
+  // once.  Validation, mass, mean and the FP16 scale per run.
+  std::vector<double> r0_copy;
+  const double* r0 = rho0;
+  {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, rho0) == cudaSuccess && pa.type == cudaMemoryTypeDevice) {
+      r0_copy.resize((size_t)total);
+      ce = cudaMemcpy(r0_copy.data(), rho0, sizeof(double) * (size_t)total, cudaMemcpyDeviceToHost);
+      if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(h, LB_KS_EINVAL, std::string("cannot read rho0: ") + cudaGetErrorString(ce)));
+      }
+      r0 = r0_copy.data();
+    } else {
+      cudaGetLastError();
+    }
+  }
   h->rho_off.resize(nruns + 1);
   h->rho_off[0] = 0;
   for (int32_t r = 0; r < nruns; ++r) h->rho_off[r + 1] = h->rho_off[r] + N[r];
   h->runs_h.resize(nruns);
   h->mass0_h.resize(nruns);
+  std::vector<int> run_err(nruns, 0);  // 1: coefficients not finite, 2: rho0 not finite
+  // everything of a run but its offset in the arena
+  auto per_run = [&](int32_t rb, int32_t re) {
+    for (int32_t r = rb; r < re; ++r) {
+      RunDesc& d = h->runs_h[r];
+      std::memset(&d, 0, sizeof(d));
+      double A[7], B[7];
+      // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
+      const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
+      if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK) {
+        run_err[r] = 1;
+        continue;
+      }
+      double mass = 0.0;
+      bool finite = true;
+      const double* rr = r0 + h->rho_off[r];
+      for (int64_t x = 0; x < N[r]; ++x) {
+        finite &= std::isfinite(rr[x]);
+        mass += rr[x];
+      }
+      if (!finite) {
+        run_err[r] = 2;
+        continue;
+      }
+      h->mass0_h[r] = mass;
+      const double rhobar = o.precision == kF64 ? 0.0 : mass / (double)N[r];
+      double gmax = 0.0;
+      if (o.precision == kF16S) {
+        for (int64_t x = 0; x < N[r]; ++x)
+          for (int i = 0; i < scheme; ++i) {
+            double v = A[i] * rr[x] + B[i] * rr[x] * rr[x] - (i == 0 ? rhobar : 0.0);
+            gmax = std::max(gmax, std::fabs(v));
+          }
+      }
+      const double scale = (o.precision == kF16S && gmax > 0.0) ? gmax : 1.0;
+      const double w = 1.0 / tau[r];
+      d.N = N[r];
+      d.reservoir = reservoir ? 1 : 0;
+      d.rho_left = reservoir ? rho_left[r] : 0.0;
+      d.rho_right = reservoir ? rho_right[r] : 0.0;
+      for (int i = 0; i < scheme; ++i) {
+        d.A[i] = A[i];
+        d.B[i] = B[i];
+        d.a[i] = A[i] * w;
+        d.b[i] = B[i] * w;
+        d.af[i] = (float)d.a[i];
+        d.bf[i] = (float)d.b[i];
+      }
+      d.r = 1.0 - w;
+      d.rhobar = rhobar;
+      d.scale = scale;
+      d.inv_scale = 1.0 / scale;
+      d.rf = (float)d.r;
+      d.rhobarf = (float)d.rhobar;
+      d.scalef = (float)scale;
+      d.inv_scalef = (float)(1.0 / scale);
+    }
+  };
+  // Large batches: contiguous groups of runs of about equal sites, one host thread each.
+  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+  const int64_t nthreads = std::max<int64_t>(1, std::min<int64_t>({hw, 32, total >> 20, (int64_t)nruns}));
+  if (nthreads == 1) {
+    per_run(0, nruns);
+  } else {
+    std::vector<std::thread> pool;
+    int32_t rb = 0;
+    for (int64_t t = 0; t < nthreads && rb < nruns; ++t) {
+      const int64_t target = total * (t + 1) / nthreads;
+      int32_t re = rb + 1;
+      while (re < nruns && h->rho_off[re] < target) ++re;
+      if (t == nthreads - 1) re = nruns;
+      pool.emplace_back(per_run, rb, re);
+      rb = re;
+    }
+    for (std::thread& th : pool) th.join();
+  }
   int64_t off = 0;
   for (int32_t r = 0; r < nruns; ++r) {
-    RunDesc& d = h->runs_h[r];
-    std::memset(&d, 0, sizeof(d));
-    double A[7], B[7];
-    // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
-    const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
-    if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK)
-      return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
-    double mass = 0.0;
-    const double* rr = r0.data() + h->rho_off[r];
-    for (int64_t x = 0; x < N[r]; ++x) {
-      if (!std::isfinite(rr[x])) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": rho0 is not finite"));
-      mass += rr[x];
-    }
-    h->mass0_h[r] = mass;
-    const double rhobar = o.precision == kF64 ? 0.0 : mass / (double)N[r];
-    double gmax = 0.0;
-    if (o.precision == kF16S) {
-      for (int64_t x = 0; x < N[r]; ++x)
-        for (int i = 0; i < scheme; ++i) {
-          double v = A[i] * rr[x] + B[i] * rr[x] * rr[x] - (i == 0 ? rhobar : 0.0);
-          gmax = std::max(gmax, std::fabs(v));
-        }
-    }
-    const double scale = (o.precision == kF16S && gmax > 0.0) ? gmax : 1.0;
-    const double w = 1.0 / tau[r];
+    if (run_err[r] == 1) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
+    if (run_err[r] == 2) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": rho0 is not finite"));
     const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
-    d.off = off + ghost;
-    d.N = N[r];
-    d.reservoir = reservoir ? 1 : 0;
-    d.rho_left = reservoir ? rho_left[r] : 0.0;
-    d.rho_right = reservoir ? rho_right[r] : 0.0;
-    for (int i = 0; i < scheme; ++i) {
-      d.A[i] = A[i];
-      d.B[i] = B[i];
-      d.a[i] = A[i] * w;
-      d.b[i] = B[i] * w;
-      d.af[i] = (float)d.a[i];
-      d.bf[i] = (float)d.b[i];
-    }
-    d.r = 1.0 - w;
-    d.rhobar = rhobar;
-    d.scale = scale;
-    d.inv_scale = 1.0 / scale;
-    d.rf = (float)d.r;
-    d.rhobarf = (float)d.rhobar;
-    d.scalef = (float)scale;
-    d.inv_scalef = (float)(1.0 / scale);
+    h->runs_h[r].off = off + ghost;
     off += align_up(N[r] + 2 * ghost, kAlign);
   }
   h->plane = std::max<int64_t>(off, kAlign);
@@ -842,7 +890,7 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
       (ce = up(h->d_stream_tile_begin, st_begin.data(), sizeof(int32_t) * st_begin.size())) != cudaSuccess ||
       (ce = up(h->d_rho_off, h->rho_off.data(), sizeof(int64_t) * h->rho_off.size())) != cudaSuccess ||
       (ce = up(h->d_mass0, h->mass0_h.data(), sizeof(double) * nruns)) != cudaSuccess ||
-      (ce = up(h->d_stage, r0.data(), sizeof(double) * (size_t)total)) != cudaSuccess ||
+      (ce = cudaMemcpy(h->d_stage, rho0, sizeof(double) * (size_t)total, cudaMemcpyDefault)) != cudaSuccess ||
       (ce = cudaMemset(h->d_flags, 0, sizeof(int))) != cudaSuccess)
     return bail(cuda_fail(h, ce, "upload"));
 
