@@ -34,10 +34,10 @@ LB_STEPS_PER_STEP = 1000
 GUARD_EVERY = 500
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the resident kernel's
 # launches in one benchmark step, from one ncu capture of the full-size default workload
-# per plan (sites per thread, threads per block, blocks per whole-lattice work group).
-# A plan not listed, or a kernel changed since the capture, reports null.
-PROFILED_TRAFFIC = {("d1q7_ensemble_4096x[256,8192]", "f32", 16, 256, 2): 866.8e6,
-                    ("d1q7_ensemble_4096x[256,8192]", "f32", 12, 384, 2): 865.0e6}
+# per plan (sites per thread, threads per block, blocks per whole-lattice work group,
+# single-block bundles merged into pairs, steps between the halo exchanges of halved
+# lattices).  A plan not listed, or a kernel changed since the capture, reports null.
+PROFILED_TRAFFIC = {("d1q7_ensemble_4096x[256,8192]", "f32", 12, 384, 2, 1, 32): 954.6e6}
 FLOP_PER_SITE_UPDATE = {7: 39, 5: 27}  # folded step, FMA = 2 flops: 6Q - 3
 # tau = 1 collapse: per c = 1..c_max two adds, an fma, an add, a mul, two fmas, then one add (FMA = 2)
 COLLAPSE_FLOP_PER_SITE_UPDATE = {7: 31, 5: 21}
@@ -58,8 +58,10 @@ def parse():
                    help="collapse: the tau = 1 rho-only step, on the ensemble at tau = 1")
     p.add_argument("--precision", default="f32", choices=["f32", "f16s", "f64"])
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
-    p.add_argument("--no-autotune", action="store_true",
-                   help="fixed default tiling (deterministic launch sequence, for profiling)")
+    p.add_argument("--autotune", action="store_true",
+                   help="let the library time candidate plans at init and keep the fastest (the default is "
+                        "its fixed plan, whose launch sequence is deterministic and profiled)")
+    p.add_argument("--no-autotune", action="store_true", help="the fixed plan (the default)")
     p.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
                    help="resident work group for whole lattices: 1 block, a 2-block cluster, 0 = auto")
     p.add_argument("--spt", type=int, default=0, help="resident sites per thread (0 = auto; for profiling a plan)")
@@ -249,11 +251,13 @@ def main():
     kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN,
             "collapse": lb.KERNEL_COLLAPSE}[args.kernel]
     opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
-                                 autotune=int(kern in (lb.KERNEL_RESIDENT, lb.KERNEL_COLLAPSE) and not args.no_autotune),
+                                 autotune=int(kern in (lb.KERNEL_RESIDENT, lb.KERNEL_COLLAPSE) and args.autotune
+                                              and not args.no_autotune),
                                  cluster_size=args.cluster, sites_per_thread=args.spt, threads_per_block=args.tpb,
                                  stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
     desc = lb.lb_ks_describe(h)
+    lanes = lb.lb_ks_describe_lanes(h)
     sites = wl.sites
 
     def barrier():
@@ -308,7 +312,9 @@ def main():
         else:
             peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12
             basis = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz (derived)"
-        plan = (wl.name, args.precision, desc["sites_per_thread"], desc["threads_per_block"], desc["cluster_size"])
+        plan = (wl.name, args.precision, desc["sites_per_thread"], desc["threads_per_block"], desc["cluster_size"],
+                max([ln["merged_single_blocks"] for ln in lanes] or [0]),
+                max([ln["pair_exchange_steps"] for ln in lanes] or [0]))
         traffic = PROFILED_TRAFFIC.get(plan) if desc["kernel"] == lb.KERNEL_RESIDENT else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": traffic, "traffic_unit": "bytes per benchmark step (ncu, DRAM read + write)",
@@ -336,6 +342,7 @@ def main():
                        "guard_every": 0 if prec == lb.F64 else GUARD_EVERY, "kernel": args.kernel,
                        "sites_per_thread": desc["sites_per_thread"], "threads_per_block": desc["threads_per_block"],
                        "steps_per_launch": k, "cluster_size": desc["cluster_size"],
+                       "plan": "autotuned" if opts.autotune else "library default", "lanes": lanes,
                        "l2": f"state {sites * Q * elem / 1e6:.0f} MB > 129 MB L2 (no flush needed)"},
             "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches)}
 

@@ -266,6 +266,25 @@ LB_KS_API int64_t lb_ks_steps_done(const lb_ks_t *h);
 LB_KS_API int lb_ks_describe(const lb_ks_t *h, int *kernel, int *sites_per_thread, int *threads_per_block,
                    int *steps_per_launch, int *cluster_size, int32_t *nruns, int64_t *total_sites);
 
+/*
+ * The register-resident plan of the handle (no counterpart in the paper): the work
+ * lists ("lanes") that run concurrently, one record of LB_KS_LANE_FIELDS int32 per
+ * lane written to lanes[8 * l .. 8 * l + 7] for l < max_lanes:
+ *   [0] blocks per work group (1, or 2 for a thread block cluster pair)
+ *   [1] work groups launched (persistent grid)
+ *   [2] bundles (work items of packed lattices) in the lane's queue
+ *   [3] steps per launch
+ *   [4] 1 if the lane holds lattice segments (longer than a work group holds)
+ *   [5] pair lanes: steps between the halo exchanges of lattices held as two halves
+ *       (0: none are)
+ *   [6] 1 if single-block bundles run two to a pair work group on this lane's queue
+ *   [7] lattices held as two halves
+ * Returns the number of lanes (0 when the handle does not run the resident kernels),
+ * or LB_KS_EINVAL (h NULL, max_lanes < 0, lanes NULL with max_lanes > 0).
+ */
+#define LB_KS_LANE_FIELDS 8
+LB_KS_API int lb_ks_describe_lanes(const lb_ks_t *h, int32_t *lanes, int max_lanes);
+
 /* Kernel launches issued by this handle since creation (a counter kept on the host). */
 LB_KS_API int64_t lb_ks_launches(const lb_ks_t *h);
 

@@ -77,6 +77,7 @@ ABI_FUNCTIONS = {
     "lb_ks_steps_done": (C.c_int64, [_P]),
     "lb_ks_describe": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
+    "lb_ks_describe_lanes": (C.c_int, [_P, C.POINTER(C.c_int32), C.c_int]),
     "lb_ks_launches": (C.c_int64, [_P]),
     "lb_ks_fma_peak": (C.c_int, [C.c_int, _PD]),
     "lb_ks_mass_energy_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int64, C.c_int64, C.c_double, C.c_double, _P,
@@ -230,6 +231,19 @@ def lb_ks_describe(h) -> dict:
                                   C.byref(tot)), h)
     return {"kernel": k.value, "sites_per_thread": s.value, "threads_per_block": t.value,
             "steps_per_launch": l.value, "cluster_size": cl.value, "nruns": nr.value, "total_sites": tot.value}
+
+
+LANE_FIELDS = ("blocks_per_group", "groups", "bundles", "steps_per_launch", "segmented", "pair_exchange_steps",
+               "merged_single_blocks", "halved_lattices")
+
+
+def lb_ks_describe_lanes(h) -> list:
+    """The resident plan: one dict per concurrent lane (empty when not resident)."""
+    buf = (C.c_int32 * (8 * len(LANE_FIELDS)))()
+    n = _load().lb_ks_describe_lanes(h, buf, 8)
+    if n < 0:
+        _check(n, h)
+    return [dict(zip(LANE_FIELDS, buf[len(LANE_FIELDS) * l:len(LANE_FIELDS) * (l + 1)])) for l in range(min(n, 8))]
 
 
 def lb_ks_launches(h) -> int:

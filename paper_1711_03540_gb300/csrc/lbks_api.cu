@@ -41,12 +41,21 @@ int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 size_t storage_bytes(int prec) { return prec == kF64 ? 8 : (prec == kF32 ? 4 : 2); }
 
+// Steps between the halo exchanges of a lattice held as two halves by a cluster pair
+// (measured on GB300: an exchange costs about two steps of a block; with 32 steps the
+// halves ran lattices of 5000-7000 sites 5-8 % faster than one ring across the pair).
+constexpr int kPairSteps = 32;
+static_assert(kPairSteps >= 1 && kPairSteps <= kPairStepsMax, "halo exchange interval");
+
 // One resident-kernel work list: bundles of pieces, launched k steps at a time on `grid` blocks.
 struct Lane {
   bool segmented = false;
   int cl = 1;           // blocks per work group (2: thread block clusters)
   double weight = 1.0;  // cost of a bundle relative to a single-block ring bundle (grid split)
   int k = 0, grid = 0, nbundles = 0;
+  int kx = 0;  // cl = 2: steps between the halo exchanges of lattice halves
+  bool merged = false;  // cl = 2: single-block bundles run two to a pair work group
+  int halves = 0;       // lattices held as two halves
   Piece* d_pieces = nullptr;
   int2* d_bundles = nullptr;
   int* d_queue = nullptr;
@@ -171,11 +180,29 @@ bool valid_opts(const lb_ks_opts& o, std::string* why) {
 
 bool has_pair_lattices(const lb_ks* h, int S, int NT);
 
+// One half of a ring of N sites for a cluster pair: own sites [x_own, x_own + len) of
+// the ring with `halo` sites on each side, lengthened on the right until it splits
+// into runs of S and S-1 sites; false if that takes more than NT threads.
+bool plan_half(int32_t r, int64_t N, int64_t x_own, int64_t len, int halo, int S, int NT, Piece* p) {
+  int64_t n = len + 2 * halo;
+  int64_t V = (n + S - 1) / S;
+  while (n <= V * (S - 1)) { ++n; V = (n + S - 1) / S; }
+  if (V > NT) return false;
+  *p = Piece{};
+  p->run = r; p->t0 = 0; p->nthr = (int)V; p->n = (int)n;
+  p->x0 = ((x_own - halo) % N + N) % N;
+  p->st_lo = halo; p->st_hi = (int)(halo + len);
+  p->halo = halo;
+  return true;
+}
+
 // Pieces of every run for (S, NT): rings (whole lattices held by at most ring_cap
 // threads: NT, or 2 NT for two-block clusters) and segments (for longer lattices,
 // held by one block each, with c_max * kseg halo sites per side); false if some
-// run cannot be held.
-bool plan_pieces(const lb_ks* h, int S, int NT, int ring_cap, int kseg, std::vector<Piece>* rings,
+// run cannot be held.  With two-block clusters and kx > 0, a lattice longer than one
+// block holds is split into two halves (consecutive in `rings`, halo c_max kx) when
+// each half with its halos fits one block, instead of one ring across both blocks.
+bool plan_pieces(const lb_ks* h, int S, int NT, int ring_cap, int kseg, int kx, std::vector<Piece>* rings,
                  std::vector<Piece>* segs) {
   rings->clear();
   segs->clear();
@@ -192,6 +219,17 @@ bool plan_pieces(const lb_ks* h, int S, int NT, int ring_cap, int kseg, std::vec
       const int64_t V = (n + S - 1) / S;
       if (V > ring_cap) break;
       if (n > V * (S - 1)) {
+        if (V > NT && kx > 0) {
+          const int halo = C * kx;
+          const int64_t NA = (N + 1) / 2, NB = N - NA;
+          Piece a{}, b{};
+          if (NB >= 2 * halo && plan_half(r, N, 0, NA, halo, S, NT, &a) && plan_half(r, N, NA, NB, halo, S, NT, &b)) {
+            rings->push_back(a);
+            rings->push_back(b);
+            ring = true;
+            break;
+          }
+        }
         Piece p{};
         p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n; p.x0 = 0; p.st_lo = 0; p.st_hi = (int)N;
         rings->push_back(p);
@@ -226,16 +264,27 @@ bool plan_pieces(const lb_ks* h, int S, int NT, int ring_cap, int kseg, std::vec
 struct Bins {
   int cap = 0;
   std::vector<std::vector<int>> members;
-  std::vector<int> used;
+  std::vector<int> used;   // threads [0, used) taken (pair work groups: the end of block 1's)
+  std::vector<int> used0;  // pair work groups: threads [0, used0) of block 0 taken
+  std::vector<int> key;    // queue order (largest first); empty: by occupied threads
 
+  // A piece never spans the block edge of a pair work group here: it goes into block
+  // 0's free threads or after block 1's taken ones.
   bool first_fit(std::vector<Piece>& pieces, int i) {
-    for (size_t b = 0; b < used.size(); ++b)
+    for (size_t b = 0; b < used.size(); ++b) {
+      if (!used0.empty() && used0[b] + pieces[i].nthr <= cap / 2) {
+        pieces[i].t0 = used0[b];
+        used0[b] += pieces[i].nthr;
+        members[b].push_back(i);
+        return true;
+      }
       if (used[b] + pieces[i].nthr <= cap) {
         pieces[i].t0 = used[b];
         used[b] += pieces[i].nthr;
         members[b].push_back(i);
         return true;
       }
+    }
     return false;
   }
   void open(std::vector<Piece>& pieces, int i) {
@@ -247,7 +296,8 @@ struct Bins {
   void emit(const std::vector<Piece>& pieces, std::vector<Piece>* ordered, std::vector<int2>* bundles) const {
     std::vector<int> order(members.size());
     for (size_t b = 0; b < members.size(); ++b) order[b] = (int)b;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return used[a] > used[b]; });
+    const std::vector<int>& kk = key.empty() ? used : key;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kk[a] > kk[b]; });
     ordered->clear();
     bundles->clear();
     for (int b : order) {
@@ -264,15 +314,59 @@ std::vector<int> by_threads_desc(const std::vector<Piece>& pieces) {
   return idx;
 }
 
-// First-fit decreasing packing of whole lattices: those longer than one block (more
-// than NT threads) each open a cluster pair (2 NT threads); the others fill the pairs'
-// spare threads first, then blocks of NT threads.
+// First-fit decreasing packing of whole lattices: a lattice held as two halves opens a
+// cluster pair (one half at the start of each block), one longer than one block (more
+// than NT threads) opens a pair as a ring across both blocks; the others fill the
+// pairs' spare threads first, then blocks of NT threads.
 void pack_rings(std::vector<Piece>& pieces, int NT, Bins* blocks, Bins* pairs) {
   blocks->cap = NT;
   pairs->cap = 2 * NT;
+  for (size_t i = 0; i + 1 < pieces.size(); ++i) {
+    if (pieces[i].halo == 0) continue;
+    pieces[i].t0 = 0;
+    pieces[i + 1].t0 = NT;
+    pairs->members.push_back({(int)i, (int)i + 1});
+    pairs->used0.push_back(pieces[i].nthr);
+    pairs->used.push_back(NT + pieces[i + 1].nthr);
+    ++i;
+  }
   for (int i : by_threads_desc(pieces)) {
-    if (pieces[i].nthr > NT) pairs->open(pieces, i);
-    else if (!pairs->first_fit(pieces, i) && !blocks->first_fit(pieces, i)) blocks->open(pieces, i);
+    if (pieces[i].halo > 0) continue;
+    if (pieces[i].nthr > NT) {
+      pairs->open(pieces, i);
+      pairs->used0.push_back(NT);
+    } else if (!pairs->first_fit(pieces, i) && !blocks->first_fit(pieces, i)) {
+      blocks->open(pieces, i);
+    }
+  }
+  pairs->key.resize(pairs->used.size());
+  for (size_t b = 0; b < pairs->used.size(); ++b) pairs->key[b] = pairs->used0[b] + pairs->used[b] - NT;
+}
+
+// One queue for every whole lattice: the single-block bundles go two to a cluster
+// pair (the second one's pieces shifted by NT threads, so no piece spans the block
+// edge and its blocks never wait on each other), queued after the pair bundles whose
+// piece spans the edge; within each kind, largest first.
+void merge_blocks_into_pairs(std::vector<Piece>& pieces, int NT, const Bins& blocks, Bins* pairs) {
+  pairs->cap = 2 * NT;
+  for (size_t b = 0; b < pairs->key.size(); ++b) pairs->key[b] += 4 * NT;
+  std::vector<int> order(blocks.members.size());
+  for (size_t b = 0; b < order.size(); ++b) order[b] = (int)b;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blocks.used[a] > blocks.used[b]; });
+  for (size_t q = 0; q < order.size(); q += 2) {
+    std::vector<int> mem = blocks.members[order[q]];
+    int used = blocks.used[order[q]];
+    if (q + 1 < order.size()) {
+      for (int i : blocks.members[order[q + 1]]) {
+        pieces[i].t0 += NT;
+        mem.push_back(i);
+      }
+      used = NT + blocks.used[order[q + 1]];
+    }
+    pairs->members.push_back(mem);
+    pairs->used.push_back(used);
+    pairs->used0.push_back(blocks.used[order[q]]);
+    pairs->key.push_back(blocks.used[order[q]]);  // the fuller of the two blocks
   }
 }
 
@@ -316,7 +410,7 @@ int upload_lane(lb_ks* h, Lane* L, const std::vector<Piece>& pieces, const Bins&
 // > 0 pin the tiling (autotuner trials); lane_weight is the cost of a pair or segment
 // bundle relative to a single-block ring bundle, used to split the blocks.
 int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, double lane_weight = 1.25,
-                   int cl_force = 0) {
+                   int cl_force = 0, int merge = -1, int kx_force = -1) {
   const bool col = h->nplanes == 1;  // the tau = 1 collapse's resident kernel
   auto supported = [&](int S, int NT) {
     return col ? collapse_resident_supported(h->Q, h->prec, S, NT) : resident_supported(h->Q, h->prec, S, NT);
@@ -342,9 +436,23 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
     if (cl == 0) cl = has_pair_lattices(h, S, NT) ? 2 : 1;
     if (col) cl = 1;  // no cluster variant of the collapse
     std::vector<Piece> rings, segs;
-    if (!plan_pieces(h, S, NT, cl * NT, kseg, &rings, &segs)) continue;
+    const int kx = cl == 2 ? (kx_force >= 0 ? kx_force : kPairSteps) : 0;
+    if (!plan_pieces(h, S, NT, cl * NT, kseg, kx, &rings, &segs)) continue;
     Bins blocks, pairs, segbins;
     pack_rings(rings, NT, &blocks, &pairs);
+    // default: one queue of pair work groups when the pairs hold most of the threads
+    int pair_thr = 0, block_thr = 0;
+    for (size_t b = 0; b < pairs.used.size(); ++b) pair_thr += pairs.used0[b] + pairs.used[b] - NT;
+    for (int u : blocks.used) block_thr += u;
+    const bool do_merge = merge >= 0 ? merge != 0 : pair_thr > block_thr;
+    bool merged = false;
+    if (do_merge && cl == 2 && !pairs.used.empty() && !blocks.used.empty()) {
+      merge_blocks_into_pairs(rings, NT, blocks, &pairs);
+      blocks = Bins{};
+      merged = true;
+    }
+    int nhalves = 0;
+    for (const Piece& p : rings) nhalves += p.halo > 0 ? 1 : 0;
     pack_blocks(segs, NT, &segbins);
     int bps = 0, max_clusters = 0;
     cudaError_t e = col ? collapse_resident_prepare(h->Q, h->prec, S, NT, &bps) : resident_prepare(h->Q, h->prec, S, NT, &bps);
@@ -364,6 +472,9 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
     }
     if (!pairs.used.empty()) {
       if ((rc = upload_lane(h, &h->lanes[h->nlanes++], rings, pairs, 2, kring, false, lane_weight))) return rc;
+      h->lanes[h->nlanes - 1].kx = nhalves ? kx : 0;
+      h->lanes[h->nlanes - 1].merged = merged;
+      h->lanes[h->nlanes - 1].halves = nhalves / 2;
     }
     if (!segbins.used.empty()) {
       if ((rc = upload_lane(h, &h->lanes[h->nlanes++], segs, segbins, 1, kseg, true, lane_weight))) return rc;
@@ -411,7 +522,7 @@ int issue_lane(lb_ks* h, const Lane& L, int64_t k, int from, bool in_place, cuda
     LBKS_CUDA(h, cudaMemsetAsync(L.d_queue, 0, sizeof(int), s), "queue reset");
     ResidentLaunch RL{h->Q, h->prec, h->S, h->NT, arena(h, cur), arena(h, dst), h->d_runs,
                       L.d_pieces, L.d_bundles, L.nbundles, L.d_queue, (int)kk, L.grid, L.cl, h->d_flags,
-                      h->nplanes == 1};
+                      h->nplanes == 1, L.kx};
     LBKS_CUDA(h, launch_resident(RL, s), "resident step");
     *nk += 1;
     cur = dst;
@@ -567,7 +678,7 @@ bool has_pair_lattices(const lb_ks* h, int S, int NT) {
 // handle's own lattices for a short run, and keeps the fastest.  Runs before the state
 // is initialised, on the zeroed arenas (the kernel's work does not depend on the values).
 int autotune_resident(lb_ks* h) {
-  struct Cand { int S, NT; double w; int cl; };
+  struct Cand { int S, NT; double w; int cl; int merge; int kx; };
   std::vector<Cand> cands;
   std::vector<std::pair<int, int>> tilings;
   const bool col = h->nplanes == 1;  // the tau = 1 collapse's resident kernel
@@ -587,7 +698,11 @@ int autotune_resident(lb_ks* h) {
       if (col && cl == 2) continue;
       if (h->opts.cluster_size && cl != h->opts.cluster_size) continue;
       if (cl == 2 && !has_pair_lattices(h, tl.first, NT)) continue;  // same plan as cl = 1
-      for (double w : {1.0, 1.25, 1.6}) cands.push_back({tl.first, tl.second, w, cl});
+      for (int kx : {kPairSteps, 0}) {
+        if (cl == 1 && kx != 0) continue;
+        for (double w : {1.0, 1.25, 1.6}) cands.push_back({tl.first, tl.second, w, cl, 0, kx});
+        if (cl == 2) cands.push_back({tl.first, tl.second, 1.0, cl, 1, kx});
+      }
     }
   }
   if (cands.empty()) return LB_KS_OK;  // keep the plan made before tuning
@@ -602,7 +717,7 @@ int autotune_resident(lb_ks* h) {
   int rc = LB_KS_OK;
   for (const Cand& c : cands) {
     release_lanes(h);
-    if (setup_resident(h, false, c.S, c.NT, c.w, c.cl) != LB_KS_OK) { cudaGetLastError(); continue; }
+    if (setup_resident(h, false, c.S, c.NT, c.w, c.cl, c.merge, c.kx) != LB_KS_OK) { cudaGetLastError(); continue; }
     if (h->nlanes < 2 && c.w != 1.0) continue;  // the split weight only matters with more than one lane
     int64_t nk = 0;
     for (int rep = 0; rep < 2 && rc == LB_KS_OK; ++rep) {  // first repetition warms up
@@ -622,7 +737,7 @@ int autotune_resident(lb_ks* h) {
   if (rc != LB_KS_OK) return rc;
   release_lanes(h);
   if (best_ms < 1e300) {
-    if ((rc = setup_resident(h, true, best.S, best.NT, best.w, best.cl)) != LB_KS_OK) return rc;
+    if ((rc = setup_resident(h, true, best.S, best.NT, best.w, best.cl, best.merge, best.kx)) != LB_KS_OK) return rc;
     h->tuned_weight = best.w;
     h->tuned_cl = best.cl;
   } else if ((rc = setup_resident(h, true)) != LB_KS_OK) {
@@ -1128,6 +1243,24 @@ int lb_ks_describe(const lb_ks_t* h, int* kernel, int* spt, int* tpb, int* spl, 
   if (nruns) *nruns = h->nruns;
   if (total) *total = h->total_sites;
   return LB_KS_OK;
+}
+
+int lb_ks_describe_lanes(const lb_ks_t* h, int32_t* lanes, int max_lanes) {
+  if (!h || max_lanes < 0 || (max_lanes > 0 && !lanes)) return LB_KS_EINVAL;
+  if (!(h->kernel == LB_KS_KERNEL_RESIDENT || h->collapse_resident)) return 0;
+  for (int l = 0; l < h->nlanes && l < max_lanes; ++l) {
+    const Lane& L = h->lanes[l];
+    int32_t* r = lanes + LB_KS_LANE_FIELDS * l;
+    r[0] = L.cl;
+    r[1] = L.grid;
+    r[2] = L.nbundles;
+    r[3] = L.segmented ? L.k : h->kmax;
+    r[4] = L.segmented ? 1 : 0;
+    r[5] = L.kx;
+    r[6] = L.merged ? 1 : 0;
+    r[7] = L.halves;
+  }
+  return h->nlanes;
 }
 
 int64_t lb_ks_launches(const lb_ks_t* h) { return h ? h->launches : -1; }

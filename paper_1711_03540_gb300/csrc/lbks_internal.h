@@ -44,7 +44,16 @@ struct Piece {
   int64_t x0;     // run-local site of loaded index 0, in [0, N)
   int32_t st_lo;  // loaded indices [st_lo, st_hi) are written back
   int32_t st_hi;
+  // > 0: one half of a lattice held by a cluster pair (the other half in the other
+  // block), with halo = c_max * kx sites on each side of its own sites [st_lo, st_hi)
+  // (st_lo = halo), refreshed from the other block every kx steps
+  int32_t halo;
+  int32_t pad_;
 };
+
+// Steps between the halo exchanges of a lattice held as two halves by a cluster pair
+// (the exchange area is sized for at most kPairStepsMax).
+constexpr int kPairStepsMax = 32;
 
 // Tile of the one-thread-per-site and streaming kernels: sites [x0, x0 + len) of one run.
 struct Tile {
@@ -95,6 +104,7 @@ struct ResidentLaunch {
   int cl = 1;  // blocks per work group: 1, or 2 (a thread block cluster)
   int* flags = nullptr;  // error flags (bit 2: a bounded wait between the blocks of a cluster ran out)
   bool collapse = false;  // the tau = 1 collapse (one stored plane) instead of the LB populations
+  int kx = 0;             // cl = 2: steps between the halo exchanges of lattice halves (Piece::halo)
 };
 bool resident_supported(int Q, int storage, int S, int NT);
 cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm);

@@ -11,18 +11,25 @@
 //
 // A work group is one thread block (CL = 1) or a cluster of CL = 2 thread
 // blocks (CL = 2) whose threads are numbered g = rank * blockDim.x + t.  This
-// holds lattices of up to 2 NT S sites whole, with no halo and no launch-edge
-// overhead, where one block would need segments.  At most one piece of a bundle
-// spans both blocks; it has exactly two links across the block edge (block 0's
-// last thread <-> block 1's first, and its own periodic wrap), so each block has
-// one thread that receives right-moving values from the other block and one that
-// receives left-moving values.  Those threads push their outgoing values into
-// the other block's shared memory with st.async, whose completion counts bytes
-// on an mbarrier there; the receiving thread waits on its own block's mbarrier
-// (a bounded wait: on time-out it sets an error flag, stops waiting and the
-// launch completes).  Each link is used in both directions every step, so a
-// push into a double-buffered slot is always ordered after the reads of that
-// slot two steps earlier.  The rest of the step uses __syncthreads only.
+// holds lattices of up to 2 NT S sites where one block would need segments
+// reloaded at every launch, in one of two forms:
+//  * two halves (Piece::halo > 0), one per block from its thread 0, each a segment
+//    of the ring with halo sites on both sides; every kx steps the blocks exchange
+//    their edge sites through shared memory and one cluster barrier (halo_exchange);
+//  * one ring across both blocks: at most one piece of a bundle spans both blocks;
+//    it has exactly two links across the block edge (block 0's last thread <->
+//    block 1's first, and its own periodic wrap), so each block has one thread that
+//    receives right-moving values from the other block and one that receives
+//    left-moving values.  Those threads push their outgoing values into the other
+//    block's shared memory with st.async, whose completion counts bytes on an
+//    mbarrier there; the receiving thread waits on its own block's mbarrier (a
+//    bounded wait: on time-out it sets an error flag, stops waiting and the launch
+//    completes).  Each link is used in both directions every step, so a push into a
+//    double-buffered slot is always ordered after the reads of that slot two steps
+//    earlier.  The rest of the step uses __syncthreads only.
+// A pair's spare threads hold whole small lattices, and a pair may also run two
+// single-block bundles side by side (no piece across the edge); the step loop
+// carries link code only for bundles that need it (resident_steps<LINK>).
 //
 // One step of Eq. LB_equation_ordinary:
 //  A. per held site: s_g = sum_i g_i, rho = rhobar + s_g, rho^2;
@@ -32,6 +39,8 @@
 //     destination register's old value has already been used); the c_i values
 //     that leave the thread go to shared memory;  g_0 = s_g - sum of the others
 //     (mass conservation; the same arithmetic, in the same order, as collide());
+//  (a ring across a cluster pair: after A, the two threads at the block edge push
+//     the values that leave the block this step, computed from A's sums;)
 //  C. one block barrier (and, for the two threads of a cluster block with a link
 //     across the block edge, the mbarrier wait), then the values entering from
 //     the neighbour thread are read (the neighbour of a piece's last thread is
@@ -85,6 +94,7 @@ struct ResidentArgs {
   int* queue;
   int ksteps;
   int* flags;  // bit 2 set when a bounded wait on the other block of a cluster ran out
+  int kx;      // cluster pairs: steps between the halo exchanges of lattice halves
 };
 
 constexpr int kFlagClusterTimeout = 2;
@@ -94,11 +104,15 @@ constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before a wait is g
 // [Q planes][NT threads x S sites], then the exchange area
 // [2 parities][2 directions][NX][NT + 2]: a column per thread for the values
 // leaving it, and two more (NT: right-moving, NT + 1: left-moving) for the values
-// the other block of a cluster pushes in.  The exchange area does not overlap the
-// staging area, since a push may land while this block is still staging.
+// the other block of a cluster pushes in, then the inbox of a lattice half
+// [2 parities][2 sides][Q][c_max kPairStepsMax]: side 0 the other half's last halo
+// sites (this half's left halo), side 1 its first ones (the right halo).  Neither
+// overlaps the staging area, since the other block may write them while this block
+// is still staging.
 __host__ __device__ constexpr int exchange_rows(int Q) { return 4 * ((Q - 1) / 2) * ((Q - 1) / 2 + 1) / 2; }
+__host__ __device__ constexpr int halo_max(int Q) { return ((Q - 1) / 2) * kPairStepsMax; }
 __host__ __device__ constexpr size_t smem_elems(int Q, int S, int NT) {
-  return (size_t)Q * S * NT + (size_t)exchange_rows(Q) * (NT + 2);
+  return (size_t)Q * S * NT + (size_t)exchange_rows(Q) * (NT + 2) + (size_t)4 * Q * halo_max(Q);
 }
 
 // ---- thread block clusters (PTX ISA: barrier.cluster, mapa, ld.shared::cluster)
@@ -127,6 +141,14 @@ __device__ __forceinline__ int ld_cluster(uint32_t addr, int) {
   int v;
   asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr));
   return v;
+}
+
+// Plain store into another block's shared memory (made visible by the next cluster barrier).
+__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
 // ---- mbarriers with transaction counts (PTX ISA: mbarrier, st.async)
@@ -168,24 +190,15 @@ __device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar)
                ::"r"(addr), "d"(v), "r"(mbar) : "memory");
 }
 
-// Edge values of one thread for the other block of a cluster, from its pre-collision
-// populations f (n held sites): the post-collision values that leave the thread to
-// the right (c_i > 0: sites n - c_i .. n - 1) or to the left (c_i < 0: sites
-// 0 .. |c_i| - 1), with the operations of phase B in the same order, stored into
-// the other block's pushed-in column (element stride ntx, row (|c|(|c|-1)/2 + j)).
+// Edge values of one thread for the other block of a cluster: the post-collision
+// values that leave the thread to the right (c_i > 0: sites n - c_i .. n - 1 of its
+// n held sites) or to the left (c_i < 0: sites 0 .. |c_i| - 1), from the
+// pre-collision populations f and phase A's rho and rho^2, with the operations of
+// phase B (which computes the same values again below), stored into the other
+// block's pushed-in column (element stride ntx, row |c|(|c|-1)/2 + j).
 template <int Q, int n, typename CT, int SF>
-__device__ __forceinline__ void push_edge_right(const CT (&f)[Q][SF], const Coef<CT, Q>& k, uint32_t col, int ntx,
-                                                uint32_t mbar) {
-  constexpr int C = cmax_of(Q);
-  CT er[C], er2[C];  // rho and rho^2 of sites n - C .. n - 1
-#pragma unroll
-  for (int m = 0; m < C; ++m) {
-    CT sg = f[0][n - C + m];
-#pragma unroll
-    for (int i = 1; i < Q; ++i) sg = add_rn(sg, f[i][n - C + m]);
-    er[m] = add_rn(k.rhobar, sg);
-    er2[m] = mul_rn(er[m], er[m]);
-  }
+__device__ __forceinline__ void push_edge_right(const CT (&f)[Q][SF], const CT (&rho)[SF], const CT (&rho2)[SF],
+                                                const Coef<CT, Q>& k, uint32_t col, int ntx, uint32_t mbar) {
   StaticFor<1, Q>::run([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     constexpr int c = speed(i);
@@ -193,8 +206,8 @@ __device__ __forceinline__ void push_edge_right(const CT (&f)[Q][SF], const Coef
       constexpr int base = c * (c - 1) / 2;
 #pragma unroll
       for (int j = 0; j < c; ++j) {
-        const int m = C - c + j;
-        const CT v = post_collision(k.r, f[i][n - c + j], er[m], er2[m], k.b[i], mul_rn(er[m], k.a[i]));
+        constexpr int s0 = n - c;
+        const CT v = post_collision(k.r, f[i][s0 + j], rho[s0 + j], rho2[s0 + j], k.b[i], mul_rn(rho[s0 + j], k.a[i]));
         st_async(col + (uint32_t)((base + j) * ntx * sizeof(CT)), v, mbar);
       }
     }
@@ -202,18 +215,8 @@ __device__ __forceinline__ void push_edge_right(const CT (&f)[Q][SF], const Coef
 }
 
 template <int Q, typename CT, int SF>
-__device__ __forceinline__ void push_edge_left(const CT (&f)[Q][SF], const Coef<CT, Q>& k, uint32_t col, int ntx,
-                                               uint32_t mbar) {
-  constexpr int C = cmax_of(Q);
-  CT er[C], er2[C];  // rho and rho^2 of sites 0 .. C - 1
-#pragma unroll
-  for (int m = 0; m < C; ++m) {
-    CT sg = f[0][m];
-#pragma unroll
-    for (int i = 1; i < Q; ++i) sg = add_rn(sg, f[i][m]);
-    er[m] = add_rn(k.rhobar, sg);
-    er2[m] = mul_rn(er[m], er[m]);
-  }
+__device__ __forceinline__ void push_edge_left(const CT (&f)[Q][SF], const CT (&rho)[SF], const CT (&rho2)[SF],
+                                               const Coef<CT, Q>& k, uint32_t col, int ntx, uint32_t mbar) {
   StaticFor<1, Q>::run([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     constexpr int c = speed(i);
@@ -223,11 +226,216 @@ __device__ __forceinline__ void push_edge_left(const CT (&f)[Q][SF], const Coef<
 #pragma unroll
       for (int j = 0; j < kk; ++j) {
         // phase B takes rho a_i of the -c plane from the +c plane before it (a_i is even in c)
-        const CT v = post_collision(k.r, f[i][j], er[j], er2[j], k.b[i], mul_rn(er[j], k.a[i - 1]));
+        const CT v = post_collision(k.r, f[i][j], rho[j], rho2[j], k.b[i], mul_rn(rho[j], k.a[i - 1]));
         st_async(col + (uint32_t)((base + j) * ntx * sizeof(CT)), v, mbar);
       }
     }
   });
+}
+
+// Link state of a block of a cluster pair whose bundle has a piece across the block
+// edge: the thread's links to the other block, this block's mbarriers (one per step
+// parity), the other block's exchange area and mbarriers in the cluster window, the
+// parities of the next phases to complete, and the time-out state of the waits.
+struct ClusterLink {
+  uint64_t* mbar = nullptr;
+  uint32_t peer_x = 0, peer_mbar = 0;
+  uint32_t ph = 0;    // bit p: parity of the next phase of mbar[p] to complete
+  bool lrem = false;  // the left neighbour is in the other block
+  bool rrem = false;  // the right neighbour is in the other block
+  bool bad = false;   // a wait ran out: stop waiting (the flag tells the host)
+  int* flags = nullptr;
+};
+
+// ksteps steps of the register-resident state f (see the kernel below for phases A-C).
+// LINK: the bundle has a piece across the edge of a cluster pair, whose boundary
+// values go through the other block's shared memory; without it the loop is that of
+// a single block (no link code in the loop, so no registers or instructions spent on it).
+template <int Q, int S, bool LINK, typename CT>
+__device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>& k, const int step0, const int ksteps,
+                                               CT* const xbase, const int NT, const int t, const bool active,
+                                               const bool full, const int lt, const int rt, ClusterLink& ln) {
+  constexpr int C = cmax_of(Q);
+  constexpr int NX = C * (C + 1) / 2;  // values leaving a thread per direction per step
+  const int NTX = NT + 2;
+  for (int step = step0; step < step0 + ksteps; ++step) {
+    const int pb = step & 1;
+    const int par = pb * 2 * NX * NTX;
+    CT* const xr = xbase + par;  // right-moving values leaving threads
+    CT* const xl = xr + NX * NTX; // left-moving values leaving threads
+    if constexpr (LINK) {
+      // this step's phase of ln.mbar[pb] completes on this arrival and on the
+      // 2 NX values the other block pushes (NX per direction)
+      if (ln.lrem && !ln.bad) mbar_arrive_expect_tx(&ln.mbar[pb], 2 * NX * (uint32_t)sizeof(CT));
+    }
+    if (active) {
+      // A. per-site sums
+      CT acc[S], rho[S], rho2[S], tt[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        CT sg = f[0][s];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) sg = add_rn(sg, f[i][s]);
+        acc[s] = sg;
+        rho[s] = add_rn(k.rhobar, sg);
+        rho2[s] = mul_rn(rho[s], rho[s]);
+      }
+      if constexpr (LINK) {
+        // Push the values this step sends across the block edge before phase B, from
+        // phase A's sums with the arithmetic of phase B (which computes them again
+        // below), so that the transfer overlaps the rest of the step.
+        if (ln.rrem) {
+          const uint32_t col = ln.peer_x + (uint32_t)((par + NT) * sizeof(CT));
+          if (full) push_edge_right<Q, S>(f, rho, rho2, k, col, NTX, ln.peer_mbar + 8u * pb);
+          else push_edge_right<Q, S - 1>(f, rho, rho2, k, col, NTX, ln.peer_mbar + 8u * pb);
+        }
+        if (ln.lrem)
+          push_edge_left<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)((par + NX * NTX + NT + 1) * sizeof(CT)), NTX,
+                            ln.peer_mbar + 8u * pb);
+      }
+      // B. plane by plane: collide, write to the destination site's register or send.
+      StaticFor<1, Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int c = speed(i);
+        constexpr int kk = c > 0 ? c : -c;
+        constexpr int base = kk * (kk - 1) / 2;
+        if constexpr (c > 0) {
+#pragma unroll
+          for (int s = S - 1; s >= 0; --s) {
+            tt[s] = mul_rn(rho[s], k.a[i]);  // shared with the -c plane that follows
+            const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
+            acc[s] = add_rn(acc[s], -v);
+            if (s + kk <= S - 2) {
+              f[i][s + kk] = v;
+            } else if (s + kk == S - 1) {
+              if (full) f[i][S - 1] = v;
+              else xr[base * NTX + t] = v;
+            } else if (s <= S - 2) {
+              xr[(base + (full ? s + kk - S : s + kk - S + 1)) * NTX + t] = v;
+            } else if (full) {  // s == S - 1 holds a site only in threads with S sites
+              xr[(base + s + kk - S) * NTX + t] = v;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
+            acc[s] = add_rn(acc[s], -v);
+            if (s >= kk) f[i][s - kk] = v;
+            else xl[(base + s) * NTX + t] = v;
+          }
+        }
+      });
+#pragma unroll
+      for (int s = 0; s < S; ++s) f[0][s] = acc[s];
+    }
+    __syncthreads();
+    if constexpr (LINK) {
+      if ((ln.lrem || ln.rrem) && !ln.bad) {
+        uint32_t it = 0;
+        while (!mbar_try_wait(&ln.mbar[pb], (ln.ph >> pb) & 1u)) {
+          if (++it == kWaitLimit) {
+            ln.bad = true;
+            if (ln.flags) atomicOr(ln.flags, kFlagClusterTimeout);
+            break;
+          }
+        }
+      }
+      ln.ph ^= 1u << pb;
+    }
+    if (active) {
+      // C. values entering from the neighbours (pushed in by the other block for
+      // a piece's threads at a block edge)
+      StaticFor<1, Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int c = speed(i);
+        constexpr int kk = c > 0 ? c : -c;
+        constexpr int base = kk * (kk - 1) / 2;
+        if constexpr (c > 0) {
+#pragma unroll
+          for (int jj = 0; jj < kk; ++jj)
+            f[i][jj] = xr[(base + jj) * NTX + lt];
+        } else {
+          // threads with S sites fill slots S-kk .. S-1, threads with S-1 sites S-1-kk .. S-2
+#pragma unroll
+          for (int jj = 0; jj < kk; ++jj) {
+            const CT v = xl[(base + jj) * NTX + rt];
+            if (full) f[i][S - kk + jj] = v;
+            else f[i][S - 1 - kk + jj] = v;
+          }
+        }
+      });
+    }
+  }
+}
+
+// Halo exchange of a lattice held as two halves by a cluster pair (Piece::halo = h;
+// `half` is this block's half, the bundle's first piece in block 0 and its second in
+// block 1, held from thread 0 of the block).  Each half runs kx steps as a segment of
+// the ring (its h halo sites on each side absorb the values its thread ring wraps in,
+// which travel at most c_max sites per step), then its first and last h own sites go
+// to the other block, whose halos they are, and come back as this block's halos.  In
+// segment coordinates the own sites are [h, h + own): sites [h, 2h) become the other
+// half's right halo, [own, own + h) its left halo; this half's left halo is [0, h) and
+// its right halo [h + own, 2h + own) (sites beyond that, when the segment was
+// lengthened to split into runs of S and S-1 sites, are farther than h from the own
+// sites and are not refreshed).
+//  a. threads holding any of those sites put all theirs into the staging area (idle
+//     between the launch edges), at their staged index (site index: the half starts
+//     at thread 0);
+//  b. all threads copy the 2 h Q outgoing values into the other block's inbox;
+//  c. after one cluster barrier, all threads copy the inbox into the halo sites of
+//     the staging area;
+//  d. the threads of a. reload their registers.
+// The inbox is double-buffered by exchange parity: a write into it is ordered after
+// the other block's reads of that buffer by the cluster barrier of the exchange between.
+// (The half's halo, own sites and threads are read from shared memory here, written at
+// the start of the bundle, so that the step loop around keeps no registers for them.)
+template <int Q, int S, typename CT>
+__device__ __forceinline__ void halo_exchange(CT (&f)[Q][S], const int (&half)[3], const bool full,
+                                              const int start, const int NT, const int t, CT* const stage,
+                                              CT* const inbox, const int par) {
+  constexpr int HM = halo_max(Q);
+  const int SS = NT * S;  // plane stride of the staging area
+  const int h = half[0], own = half[1];
+  const int n = full ? S : S - 1;
+  const bool mine = t < half[2];  // the half is held from thread 0 of the block
+  const bool edge = mine && (start < 2 * h || start + n > own);
+  if (edge) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (s < n) stage[i * SS + start + s] = f[i][s];
+  }
+  __syncthreads();
+  const uint32_t peer_inbox = cluster_addr(inbox, cluster_rank() ^ 1);
+  for (int tt = t; tt < 2 * h; tt += NT) {
+    // tt < h: own site h + tt -> the other half's right halo (side 1); else own site
+    // own + tt - h -> its left halo (side 0)
+    const int side = tt < h ? 1 : 0;
+    const int m = tt < h ? tt : tt - h;
+    const int src = tt < h ? h + m : own + m;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      st_cluster(peer_inbox + (uint32_t)((((par * 2 + side) * Q + i) * HM + m) * sizeof(CT)), stage[i * SS + src]);
+  }
+  cluster_barrier();
+  for (int tt = t; tt < 2 * h; tt += NT) {
+    const int side = tt < h ? 0 : 1;
+    const int m = tt < h ? tt : tt - h;
+    const int dst = tt < h ? m : h + own + m;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) stage[i * SS + dst] = inbox[((par * 2 + side) * Q + i) * HM + m];
+  }
+  __syncthreads();
+  if (edge) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        if (s < n) f[i][s] = stage[i * SS + start + s];
+  }
 }
 
 template <int Q, int ST, int S, int CL>
@@ -242,22 +450,27 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
   const int NTX = NT + 2;                              // exchange-area row length
   CT* const stage = reinterpret_cast<CT*>(smem_raw);   // [Q][NT * S] at the launch edges
   CT* const xbase = stage + Q * S * NT;                // [parity][R|L][NX][NT + 2]
+  CT* const inbox = xbase + exchange_rows(Q) * NTX;    // [parity][L|R halo][Q][c_max kPairStepsMax]
   __shared__ int s_bundle;
+  __shared__ int s_half[3];                            // CL = 2: halo, own sites, threads of this block's half
   __shared__ __align__(8) uint64_t s_mbar[2];          // CL = 2: counts the pushed bytes, one per parity
+  // CL = 2, kept in shared memory between the bundles whose pieces span the block edge
+  // (so that no registers are held for them while other bundles run): bit p of s_ph is
+  // the parity of the next phase of s_mbar[p] to complete; s_bad: a wait ran out, stop
+  // waiting (the flag tells the host)
+  __shared__ uint32_t s_ph;
+  __shared__ int s_bad;
   const int t = threadIdx.x;
   const int rank = CL == 1 ? 0 : cluster_rank();
   const int g = rank * NT + t;  // thread index in the work group
-  uint32_t peer_x = 0, peer_mbar = 0;  // the other block's exchange area and mbarriers
-  uint32_t ph = 0;   // bit p: parity of the next phase of s_mbar[p] to complete
-  bool bad = false;  // a wait ran out: stop waiting (the flag tells the host)
   if constexpr (CL == 2) {
     if (t == 0) {
       mbar_init(&s_mbar[0], 1);
       mbar_init(&s_mbar[1], 1);
       fence_mbar_init();
+      s_ph = 0;
+      s_bad = 0;
     }
-    peer_x = cluster_addr(xbase, rank ^ 1);
-    peer_mbar = cluster_addr(s_mbar, rank ^ 1);
   }
 
   for (;;) {
@@ -283,6 +496,17 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       if (g >= t0 && g < t0 + a.pieces[p].nthr) { pidx = p; break; }
     }
     const bool active = pidx >= 0;
+    if constexpr (CL == 2) {
+      // a lattice held as two halves: the first piece of the bundle in block 0, the
+      // second in block 1, each from thread 0 (read after the load phase's barriers)
+      if (t == 0) {
+        const Piece& hp = a.pieces[bd.x + rank];
+        const bool hv = bd.y > rank && hp.halo > 0;
+        s_half[0] = hv ? hp.halo : 0;
+        s_half[1] = hv ? hp.st_hi - hp.st_lo : 0;
+        s_half[2] = hv ? hp.nthr : 0;
+      }
+    }
 
     CT f[Q][S];
     Coef<CT, Q> k;
@@ -345,114 +569,43 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
     }
     // block-uniform: does a piece of this bundle span both blocks (then this block
     // has one thread with lrem and one with rrem, possibly the same thread)
-    bool span = false;
-    if constexpr (CL == 2) span = __syncthreads_or(lrem || rrem);
-    else __syncthreads();
-
-    for (int step = 0; step < a.ksteps; ++step) {
-      const int pb = step & 1;
-      const int par = pb * 2 * NX * NTX;
-      CT* const xr = xbase + par;  // right-moving values leaving threads
-      CT* const xl = xr + NX * NTX; // left-moving values leaving threads
-      if constexpr (CL == 2) {
-        // this step's phase of s_mbar[pb] completes on this arrival and on the
-        // 2 NX values the other block pushes (NX per direction)
-        if (lrem && !bad) mbar_arrive_expect_tx(&s_mbar[pb], 2 * NX * (uint32_t)sizeof(CT));
-        // Push the values this step sends across the block edge first, computed from
-        // the pre-collision state with the arithmetic of phase B (which computes them
-        // again below), so that the transfer overlaps the step's work.
-        if (rrem) {
-          if (full) push_edge_right<Q, S>(f, k, peer_x + (uint32_t)((par + NT) * sizeof(CT)), NTX, peer_mbar + 8u * pb);
-          else push_edge_right<Q, S - 1>(f, k, peer_x + (uint32_t)((par + NT) * sizeof(CT)), NTX, peer_mbar + 8u * pb);
-        }
-        if (lrem) push_edge_left<Q>(f, k, peer_x + (uint32_t)((par + NX * NTX + NT + 1) * sizeof(CT)), NTX,
-                                    peer_mbar + 8u * pb);
-      }
-      if (active) {
-        // A. per-site sums
-        CT acc[S], rho[S], rho2[S], tt[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-          CT sg = f[0][s];
-#pragma unroll
-          for (int i = 1; i < Q; ++i) sg = add_rn(sg, f[i][s]);
-          acc[s] = sg;
-          rho[s] = add_rn(k.rhobar, sg);
-          rho2[s] = mul_rn(rho[s], rho[s]);
-        }
-        // B. plane by plane: collide, write to the destination site's register or send.
-        StaticFor<1, Q>::run([&](auto ic) {
-          constexpr int i = decltype(ic)::value;
-          constexpr int c = speed(i);
-          constexpr int kk = c > 0 ? c : -c;
-          constexpr int base = kk * (kk - 1) / 2;
-          if constexpr (c > 0) {
-#pragma unroll
-            for (int s = S - 1; s >= 0; --s) {
-              tt[s] = mul_rn(rho[s], k.a[i]);  // shared with the -c plane that follows
-              const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
-              acc[s] = add_rn(acc[s], -v);
-              if (s + kk <= S - 2) {
-                f[i][s + kk] = v;
-              } else if (s + kk == S - 1) {
-                if (full) f[i][S - 1] = v;
-                else xr[base * NTX + t] = v;
-              } else if (s <= S - 2) {
-                xr[(base + (full ? s + kk - S : s + kk - S + 1)) * NTX + t] = v;
-              } else if (full) {  // s == S - 1 holds a site only in threads with S sites
-                xr[(base + s + kk - S) * NTX + t] = v;
-              }
-            }
-          } else {
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-              const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
-              acc[s] = add_rn(acc[s], -v);
-              if (s >= kk) f[i][s - kk] = v;
-              else xl[(base + s) * NTX + t] = v;
-            }
-          }
-        });
-#pragma unroll
-        for (int s = 0; s < S; ++s) f[0][s] = acc[s];
-      }
+    bool span = false, halves = false;
+    if constexpr (CL == 2) {
+      span = __syncthreads_or(lrem || rrem);
+      // block-uniform: the bundle holds a lattice as two halves (one per block)
+      halves = __syncthreads_or(active && pc.halo > 0);
+    } else {
       __syncthreads();
-      if constexpr (CL == 2) {
-        if ((lrem || rrem) && !bad) {
-          uint32_t it = 0;
-          while (!mbar_try_wait(&s_mbar[pb], (ph >> pb) & 1u)) {
-            if (++it == kWaitLimit) {
-              bad = true;
-              if (a.flags) atomicOr(a.flags, kFlagClusterTimeout);
-              break;
-            }
-          }
+    }
+
+    ClusterLink ln;
+    if constexpr (CL == 2) {
+      if (span) {
+        ln.mbar = s_mbar;
+        ln.peer_x = cluster_addr(xbase, rank ^ 1);
+        ln.peer_mbar = cluster_addr(s_mbar, rank ^ 1);
+        ln.ph = s_ph;
+        ln.lrem = lrem;
+        ln.rrem = rrem;
+        ln.bad = s_bad != 0;
+        ln.flags = a.flags;
+        resident_steps<Q, S, true>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
+        // every thread toggled the same parities; the next write follows the barriers
+        // of the store phase below
+        if (t == 0) s_ph = ln.ph;
+        if (ln.bad) s_bad = 1;
+      } else if (halves && a.kx > 0) {
+        for (int s0 = 0; s0 < a.ksteps; s0 += a.kx) {
+          const int kk = min(a.kx, a.ksteps - s0);
+          resident_steps<Q, S, false>(f, k, s0, kk, xbase, NT, t, active, full, lt, rt, ln);
+          if (s0 + kk < a.ksteps)
+            halo_exchange<Q, S>(f, s_half, full, start, NT, t, stage, inbox, (s0 / a.kx) & 1);
         }
-        if (span) ph ^= 1u << pb;
+      } else {
+        resident_steps<Q, S, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
       }
-      if (active) {
-        // C. values entering from the neighbours (pushed in by the other block for
-        // a piece's threads at a block edge)
-        StaticFor<1, Q>::run([&](auto ic) {
-          constexpr int i = decltype(ic)::value;
-          constexpr int c = speed(i);
-          constexpr int kk = c > 0 ? c : -c;
-          constexpr int base = kk * (kk - 1) / 2;
-          if constexpr (c > 0) {
-#pragma unroll
-            for (int jj = 0; jj < kk; ++jj)
-              f[i][jj] = xr[(base + jj) * NTX + lt];
-          } else {
-            // threads with S sites fill slots S-kk .. S-1, threads with S-1 sites S-1-kk .. S-2
-#pragma unroll
-            for (int jj = 0; jj < kk; ++jj) {
-              const CT v = xl[(base + jj) * NTX + rt];
-              if (full) f[i][S - kk + jj] = v;
-              else f[i][S - 1 - kk + jj] = v;
-            }
-          }
-        });
-      }
+    } else {
+      resident_steps<Q, S, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
     }
     __syncthreads();
 

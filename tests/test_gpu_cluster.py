@@ -1,6 +1,7 @@
 """GPU parity of the resident kernel's two-block work groups (thread block
 clusters of 2, opts.cluster_size = 2): whole lattices of up to 2 NT S sites held
-across both blocks, boundary values read from the other block's shared memory.
+across both blocks (boundary values pushed into the other block's shared memory
+every step), or as two haloed halves whose halos are exchanged every 32 steps.
 
 * FP64: the oracle within 1e-12 relative (the same bar as the other families).
 * With equal storage precision every family and work-group size runs the same
@@ -85,6 +86,92 @@ def test_cluster_pairs_equal_single_block_segments_bitwise(lb, prec, S, NT):
     assert d1["cluster_size"] == 1 and d2["cluster_size"] == 2
     np.testing.assert_array_equal(one, plain)
     np.testing.assert_array_equal(two, plain)
+
+
+# S = 4, NT = 64.  Enough pair lattices that the pairs hold most of the threads (the
+# library then runs every whole lattice from one queue of pair work groups), and enough
+# one-block lattices to leave single-block bundles after the pairs' spare threads are
+# filled: five of them (odd) in the first set, four in the second.
+MERGED_NS = [[257, 300, 385, 449, 511, 512, 400, 480, 256, 253, 192, 193, 250, 240, 200, 37, 100],
+             [257, 300, 385, 449, 511, 512, 400, 480, 256, 253, 193, 250, 240, 200, 37, 100]]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("which", [0, 1])
+def test_single_block_bundles_merged_into_pairs_bitwise(lb, prec, which):
+    """Single-block bundles go two to a pair (the second block's pieces shifted by NT
+    threads, no piece across the block edge), on one queue with the pair bundles;
+    results equal the one-block plan and the plain kernel bitwise."""
+    S, NT = 4, 64
+    Ns = np.array(MERGED_NS[which], dtype=np.int64)
+    r0, taus = _inputs(Ns, 76 + which)
+    common = dict(kernel=3, precision=prec, sites_per_thread=S, threads_per_block=NT)
+    one, d1 = run_gpu(lb, 7, Ns, r0, 300, taus, cluster_size=1, **common)
+    two, d2 = run_gpu(lb, 7, Ns, r0, 300, taus, cluster_size=2, **common)
+    plain, _ = run_gpu(lb, 7, Ns, r0, 300, taus, kernel=1, precision=prec)
+    assert d1["cluster_size"] == 1 and d2["cluster_size"] == 2
+    np.testing.assert_array_equal(one, plain)
+    np.testing.assert_array_equal(two, plain)
+
+
+# S = 8, NT = 256: one block holds 2048 sites.  A lattice longer than that is held as
+# two halves, one per block of the pair, each with c_max * 32 halo sites per side
+# (refreshed from the other block every 32 steps) when a half with its halos fits a
+# block: up to 3712 sites for D1Q7 (halo 96), 3840 for D1Q5 (halo 64); longer ones run
+# as one ring across both blocks.  Small lattices fill the spare threads of both blocks.
+HALVES_NS = [2049, 2500, 3001, 3500, 3712, 3900, 4096, 300, 77, 1000, 13]
+
+
+@pytest.mark.parametrize("Q", [5, 7])
+def test_cluster_halves_fp64_match_oracle(lb, Q):
+    Ns = np.array(HALVES_NS, dtype=np.int64)
+    r0, taus = _inputs(Ns, 81, tau_min=1.0)
+    n, dx, dt = 300, 0.4, 2e-4
+    ref, _ = ora.run_batch(Q, Ns, np.full(Ns.size, dx), np.full(Ns.size, dt), taus, r0, n)
+    out, desc = run_gpu(lb, Q, Ns, r0, n, taus, dx=dx, dt=dt, kernel=3, sites_per_thread=8, threads_per_block=256,
+                        cluster_size=2)
+    assert desc["kernel"] == 3 and desc["cluster_size"] == 2
+    assert np.max(np.abs(out - ref)) <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("recentre", [0, 50])
+def test_cluster_halves_bitwise_with_launch_lengths(lb, recentre):
+    """F32: halves equal the plain kernel bitwise, with 1000-step launches (31 exchanges
+    and a final 8-step chunk) and with 50-step launches between guards (one exchange
+    and an 18-step chunk), over several graph replays."""
+    Ns = np.array(HALVES_NS, dtype=np.int64)
+    r0, taus = _inputs(Ns, 82)
+    r0 = 0.01 * r0
+    halves, d = run_gpu(lb, 7, Ns, r0, 1000, taus, kernel=3, precision=1, sites_per_thread=8, threads_per_block=256,
+                        cluster_size=2, recentre_every=recentre)
+    plain, _ = run_gpu(lb, 7, Ns, r0, 1000, taus, kernel=1, precision=1, recentre_every=recentre)
+    assert d["cluster_size"] == 2
+    np.testing.assert_array_equal(halves, plain)
+
+
+def test_cluster_halves_checkpoint(lb):
+    """A checkpoint taken between launches of a run with halves restores it bitwise."""
+    Ns = np.array(HALVES_NS[:7], dtype=np.int64)
+    r0, taus = _inputs(Ns, 83)
+    r0 = 0.01 * r0
+    opts = dict(kernel=3, precision=1, sites_per_thread=8, threads_per_block=256, cluster_size=2, recentre_every=100)
+    ref, _ = run_gpu(lb, 7, Ns, r0, 400, taus, **opts)
+    h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(Ns.size, 1e-4), taus, r0, lb.lb_ks_default_opts(**opts))
+    try:
+        lb.lb_ks_step(h, 200)
+        blob = np.empty(lb.lb_ks_state_bytes(h), dtype=np.uint8)
+        lb.lb_ks_save(h, blob)
+        lb.lb_ks_step(h, 200)
+        a = np.empty(r0.size)
+        lb.lb_ks_rho(h, a)
+        lb.lb_ks_load(h, blob)
+        lb.lb_ks_step(h, 200)
+        b = np.empty(r0.size)
+        lb.lb_ks_rho(h, b)
+    finally:
+        lb.lb_ks_free(h)
+    np.testing.assert_array_equal(a, ref)
+    np.testing.assert_array_equal(b, ref)
 
 
 def test_cluster_f16s_one_step_per_launch_equals_stream(lb):
