@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -128,13 +129,51 @@ int cuda_fail(lb_ks* h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
   } while (0)
 
+// Device memory of the handles comes from one stream-ordered pool per device, created
+// on first use, which keeps up to kPoolKeep bytes reserved once they are freed: a
+// program that creates and frees handles repeatedly (one per job) then reuses that
+// memory instead of paying cudaMalloc and cudaFree for its arenas every time.
+constexpr uint64_t kPoolKeep = 4ull << 30;
+
+cudaError_t handle_pool(cudaMemPool_t* out) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+    uint64_t keep = kPoolKeep;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    pools[dev] = pool;
+  }
+  *out = pools[dev];
+  return cudaSuccess;
+}
+
 template <typename T>
 int dalloc(lb_ks* h, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = handle_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), count * sizeof(T), pool, h->stream);
+  // usable on every stream of the handle (and by synchronous copies) from here on
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    if (*p) cudaFreeAsync(*p, h->stream);
+    *p = nullptr;
     return fail(h, LB_KS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
   }
   h->allocations.push_back(*p);
@@ -149,7 +188,7 @@ void dfree(lb_ks* h, T** p) {
       h->allocations.erase(h->allocations.begin() + i);
       break;
     }
-  cudaFree(*p);
+  cudaFreeAsync(*p, h->stream);  // (the handle's streams are idle or joined to h->stream here)
   *p = nullptr;
 }
 
@@ -263,34 +302,65 @@ bool plan_pieces(const lb_ks* h, int S, int NT, int ring_cap, int kseg, int kx, 
 // groups of `cap` threads.
 struct Bins {
   int cap = 0;
+  bool pair = false;  // pair work groups: block 0 is threads [0, cap/2), block 1 the rest
   std::vector<std::vector<int>> members;
   std::vector<int> used;   // threads [0, used) taken (pair work groups: the end of block 1's)
   std::vector<int> used0;  // pair work groups: threads [0, used0) of block 0 taken
   std::vector<int> key;    // queue order (largest first); empty: by occupied threads
+  // Segment tree of the largest free run (block 0's or block 1's) over the groups, so
+  // that first fit finds the first group with room in O(log groups).
+  std::vector<int> tree;
+  size_t tn = 0;
 
-  // A piece never spans the block edge of a pair work group here: it goes into block
-  // 0's free threads or after block 1's taken ones.
-  bool first_fit(std::vector<Piece>& pieces, int i) {
-    for (size_t b = 0; b < used.size(); ++b) {
-      if (!used0.empty() && used0[b] + pieces[i].nthr <= cap / 2) {
-        pieces[i].t0 = used0[b];
-        used0[b] += pieces[i].nthr;
-        members[b].push_back(i);
-        return true;
-      }
-      if (used[b] + pieces[i].nthr <= cap) {
-        pieces[i].t0 = used[b];
-        used[b] += pieces[i].nthr;
-        members[b].push_back(i);
-        return true;
-      }
+  int room(size_t b) const {
+    int f = cap - used[b];
+    if (pair) f = std::max(f, cap / 2 - used0[b]);
+    return f;
+  }
+  void fix(size_t b) {
+    if (b >= tn) {
+      tn = std::max<size_t>(64, 2 * tn);
+      while (tn <= b) tn *= 2;
+      tree.assign(2 * tn, -1);
+      for (size_t q = 0; q < used.size(); ++q) tree[tn + q] = room(q);
+      for (size_t p = tn - 1; p >= 1; --p) tree[p] = std::max(tree[2 * p], tree[2 * p + 1]);
+      return;
     }
-    return false;
+    size_t p = tn + b;
+    tree[p] = room(b);
+    for (p >>= 1; p >= 1; p >>= 1) tree[p] = std::max(tree[2 * p], tree[2 * p + 1]);
+  }
+  // A new group holding pieces `mem`, with u0 threads of block 0 (pair groups) and
+  // threads [0, u) (pair groups: block 1's up to u) taken.
+  void add(std::vector<int> mem, int u0, int u) {
+    members.push_back(std::move(mem));
+    used.push_back(u);
+    if (pair) used0.push_back(u0);
+    fix(used.size() - 1);
+  }
+  // First fit: the first group with room for the piece.  A piece never spans the
+  // block edge of a pair work group here: it goes into block 0's free threads or
+  // after block 1's taken ones.
+  bool first_fit(std::vector<Piece>& pieces, int i) {
+    const int need = pieces[i].nthr;
+    if (tn == 0 || tree[1] < need) return false;
+    size_t p = 1;
+    while (p < tn) p = tree[2 * p] >= need ? 2 * p : 2 * p + 1;
+    const size_t b = p - tn;
+    if (pair && used0[b] + need <= cap / 2) {
+      pieces[i].t0 = used0[b];
+      used0[b] += need;
+    } else {
+      pieces[i].t0 = used[b];
+      used[b] += need;
+    }
+    members[b].push_back(i);
+    fix(b);
+    return true;
   }
   void open(std::vector<Piece>& pieces, int i) {
     pieces[i].t0 = 0;
-    members.push_back({i});
-    used.push_back(pieces[i].nthr);
+    add({i}, 0, pieces[i].nthr);
   }
   // bundles in decreasing order of occupied threads (longest first)
   void emit(const std::vector<Piece>& pieces, std::vector<Piece>* ordered, std::vector<int2>* bundles) const {
@@ -321,20 +391,19 @@ std::vector<int> by_threads_desc(const std::vector<Piece>& pieces) {
 void pack_rings(std::vector<Piece>& pieces, int NT, Bins* blocks, Bins* pairs) {
   blocks->cap = NT;
   pairs->cap = 2 * NT;
+  pairs->pair = true;
   for (size_t i = 0; i + 1 < pieces.size(); ++i) {
     if (pieces[i].halo == 0) continue;
     pieces[i].t0 = 0;
     pieces[i + 1].t0 = NT;
-    pairs->members.push_back({(int)i, (int)i + 1});
-    pairs->used0.push_back(pieces[i].nthr);
-    pairs->used.push_back(NT + pieces[i + 1].nthr);
+    pairs->add({(int)i, (int)i + 1}, pieces[i].nthr, NT + pieces[i + 1].nthr);
     ++i;
   }
   for (int i : by_threads_desc(pieces)) {
     if (pieces[i].halo > 0) continue;
     if (pieces[i].nthr > NT) {
-      pairs->open(pieces, i);
-      pairs->used0.push_back(NT);
+      pieces[i].t0 = 0;
+      pairs->add({i}, NT, pieces[i].nthr);
     } else if (!pairs->first_fit(pieces, i) && !blocks->first_fit(pieces, i)) {
       blocks->open(pieces, i);
     }
@@ -347,6 +416,7 @@ void pack_rings(std::vector<Piece>& pieces, int NT, Bins* blocks, Bins* pairs) {
 // pair (the second one's pieces shifted by NT threads, so no piece spans the block
 // edge and its blocks never wait on each other), queued after the pair bundles whose
 // piece spans the edge; within each kind, largest first.
+// (Groups appended here take no further pieces.)
 void merge_blocks_into_pairs(std::vector<Piece>& pieces, int NT, const Bins& blocks, Bins* pairs) {
   pairs->cap = 2 * NT;
   for (size_t b = 0; b < pairs->key.size(); ++b) pairs->key[b] += 4 * NT;
@@ -889,13 +959,23 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
         run_err[r] = 1;
         continue;
       }
-      double mass = 0.0;
+      // four interleaved partial sums (a single dependent chain is latency-bound),
+      // in a fixed order, so the result does not depend on the threads used
+      double m4[4] = {0.0, 0.0, 0.0, 0.0};
       bool finite = true;
       const double* rr = r0 + h->rho_off[r];
-      for (int64_t x = 0; x < N[r]; ++x) {
-        finite &= std::isfinite(rr[x]);
-        mass += rr[x];
+      int64_t x = 0;
+      for (; x + 4 <= N[r]; x += 4) {
+        for (int q = 0; q < 4; ++q) {
+          finite &= std::isfinite(rr[x + q]);
+          m4[q] += rr[x + q];
+        }
       }
+      for (; x < N[r]; ++x) {
+        finite &= std::isfinite(rr[x]);
+        m4[0] += rr[x];
+      }
+      const double mass = (m4[0] + m4[1]) + (m4[2] + m4[3]);
       if (!finite) {
         run_err[r] = 2;
         continue;
@@ -1271,7 +1351,7 @@ void lb_ks_free(lb_ks_t* h) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   for (cudaStream_t ss : h->side_stream)
     if (ss) cudaStreamSynchronize(ss);
-  for (void* p : h->allocations) cudaFree(p);
+  for (void* p : h->allocations) cudaFreeAsync(p, h->stream);  // back to the pool, in stream order
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int l = 0; l < 2; ++l) {
     if (h->side_stream[l]) cudaStreamDestroy(h->side_stream[l]);

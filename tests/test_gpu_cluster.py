@@ -38,6 +38,7 @@ def run_gpu(lb, Q, Ns, r0, n, taus, dx=0.1, dt=1e-4, **opts):
         out = np.empty(int(Ns.sum()))
         lb.lb_ks_rho(h, out)
         desc = lb.lb_ks_describe(h)
+        desc["lanes"] = lb.lb_ks_describe_lanes(h)
     finally:
         lb.lb_ks_free(h)
     return out, desc
@@ -110,6 +111,8 @@ def test_single_block_bundles_merged_into_pairs_bitwise(lb, prec, which):
     two, d2 = run_gpu(lb, 7, Ns, r0, 300, taus, cluster_size=2, **common)
     plain, _ = run_gpu(lb, 7, Ns, r0, 300, taus, kernel=1, precision=prec)
     assert d1["cluster_size"] == 1 and d2["cluster_size"] == 2
+    assert len(d2["lanes"]) == 1 and d2["lanes"][0]["merged_single_blocks"] == 1
+    assert all(ln["merged_single_blocks"] == 0 for ln in d1["lanes"])
     np.testing.assert_array_equal(one, plain)
     np.testing.assert_array_equal(two, plain)
 
@@ -146,6 +149,10 @@ def test_cluster_halves_bitwise_with_launch_lengths(lb, recentre):
                         cluster_size=2, recentre_every=recentre)
     plain, _ = run_gpu(lb, 7, Ns, r0, 1000, taus, kernel=1, precision=1, recentre_every=recentre)
     assert d["cluster_size"] == 2
+    # 2049 .. 3712 sites as halves, 3900 and 4096 as rings across the pair
+    (pl,) = [ln for ln in d["lanes"] if ln["blocks_per_group"] == 2]
+    assert pl["halved_lattices"] == 5 and pl["pair_exchange_steps"] == 32
+    assert pl["steps_per_launch"] == (1000 if recentre == 0 else 50)
     np.testing.assert_array_equal(halves, plain)
 
 
