@@ -1014,9 +1014,10 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
       d.inv_scalef = (float)(1.0 / scale);
     }
   };
-  // Large batches: contiguous groups of runs of about equal sites, one host thread each.
+  // Large batches: contiguous groups of runs of about equal sites (at least 2^18), one
+  // host thread each.
   const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
-  const int64_t nthreads = std::max<int64_t>(1, std::min<int64_t>({hw, 32, total >> 20, (int64_t)nruns}));
+  const int64_t nthreads = std::max<int64_t>(1, std::min<int64_t>({hw, 32, total >> 18, (int64_t)nruns}));
   if (nthreads == 1) {
     per_run(0, nruns);
   } else {
@@ -1085,9 +1086,25 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
       (ce = up(h->d_stream_tile_begin, st_begin.data(), sizeof(int32_t) * st_begin.size())) != cudaSuccess ||
       (ce = up(h->d_rho_off, h->rho_off.data(), sizeof(int64_t) * h->rho_off.size())) != cudaSuccess ||
       (ce = up(h->d_mass0, h->mass0_h.data(), sizeof(double) * nruns)) != cudaSuccess ||
-      (ce = cudaMemcpy(h->d_stage, rho0, sizeof(double) * (size_t)total, cudaMemcpyDefault)) != cudaSuccess ||
       (ce = cudaMemset(h->d_flags, 0, sizeof(int))) != cudaSuccess)
     return bail(cuda_fail(h, ce, "upload"));
+  // rho0 goes up on the handle's stream while the host plans below; the init kernels
+  // follow it in stream order, and create() waits for the copy (not for them) before
+  // it returns, so the caller's buffer is free again when it does.
+  struct CopyWait {
+    cudaEvent_t ev = nullptr;
+    ~CopyWait() {
+      if (ev) {
+        cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+      }
+    }
+  } staged;
+  if ((ce = cudaMemcpyAsync(h->d_stage, rho0, sizeof(double) * (size_t)total, cudaMemcpyDefault, h->stream)) !=
+          cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&staged.ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventRecord(staged.ev, h->stream)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "upload rho0"));
 
   // Kernel family.
   int kern = o.kernel;
