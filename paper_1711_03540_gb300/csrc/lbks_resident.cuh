@@ -438,6 +438,39 @@ __device__ __forceinline__ void halo_exchange(CT (&f)[Q][S], const int (&half)[3
   }
 }
 
+// Where a piece's sites sit, for the thread g = rank * NT + t of its work group: the
+// thread's index j in the piece and its first site, whether it holds S sites, the
+// piece's threads in this block [jlo, jlo + Vr) and their sites [lo_site, hi_site), the
+// staged index of piece site li (sbase + li), and the run-local site of this thread's
+// first launch-edge access.  Computed before the load and again, from the piece read
+// anew, before the store, so that none of it is held in registers through the steps.
+struct PieceGeom {
+  int64_t N, x_first;
+  int j, start, jlo, Vr, lo_site, hi_site, sbase;
+  bool full;
+};
+
+template <int S>
+__device__ __forceinline__ PieceGeom piece_geom(const Piece& pc, const int64_t N, const int g, const int rank,
+                                                const int NT) {
+  PieceGeom G;
+  const int V = pc.nthr;
+  const int mfull = pc.n - V * (S - 1);  // threads holding S sites; the rest hold S-1
+  auto site_start = [&](int jj) { return jj < mfull ? jj * S : mfull * S + (jj - mfull) * (S - 1); };
+  G.N = N;
+  G.j = g - pc.t0;
+  G.full = G.j < mfull;
+  G.start = site_start(G.j);
+  G.jlo = max(0, rank * NT - pc.t0);
+  const int jhi = min(V, rank * NT + NT - pc.t0);
+  G.Vr = jhi - G.jlo;
+  G.lo_site = site_start(G.jlo);
+  G.hi_site = site_start(jhi);
+  G.sbase = (pc.t0 + G.jlo - rank * NT) * S - G.lo_site;
+  G.x_first = (pc.x0 + G.lo_site + (G.j - G.jlo)) % N;
+  return G;
+}
+
 template <int Q, int ST, int S, int CL>
 __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_kernel(const ResidentArgs a) {
   static_assert(CL == 1 || CL == 2, "work groups are one block or a pair of blocks");
@@ -511,25 +544,19 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
     CT f[Q][S];
     Coef<CT, Q> k;
     bool full = true;
-    int j = 0, start = 0;
+    int start = 0;
     int lt = t, rt = t;                    // exchange columns the incoming values are read from
     bool lrem = false, rrem = false;       // left / right neighbour in the other block
-    int jlo = 0, Vr = 1, lo_site = 0, hi_site = 0, sbase = 0;
-    Piece pc{};
-    int64_t N = 1, x_first = 0;
+    PieceGeom G{};
     const T* fs = nullptr;
-    T* fd = nullptr;
     if (active) {
-      pc = a.pieces[pidx];
+      const Piece pc = a.pieces[pidx];
       const RunDesc& d = a.runs[pc.run];
       k = load_coef<CT, Q>(d);
-      N = d.N;
-      const int V = pc.nthr;
-      j = g - pc.t0;
-      const int mfull = pc.n - V * (S - 1);  // threads holding S sites; the rest hold S-1
-      auto site_start = [&](int jj) { return jj < mfull ? jj * S : mfull * S + (jj - mfull) * (S - 1); };
-      full = j < mfull;
-      start = site_start(j);
+      G = piece_geom<S>(pc, d.N, g, rank, NT);
+      full = G.full;
+      start = G.start;
+      const int V = pc.nthr, j = G.j;
       const int lg = pc.t0 + (j == 0 ? V - 1 : j - 1);
       const int rg = pc.t0 + (j == V - 1 ? 0 : j + 1);
       const int lrank = CL == 1 ? 0 : lg / NT;
@@ -538,26 +565,18 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       rrem = rrank != rank;
       lt = lrem ? NT : lg - lrank * NT;        // pushed-in columns for a neighbour in the other block
       rt = rrem ? NT + 1 : rg - rrank * NT;
-      // the piece's threads in this block, and the sites they hold
-      jlo = max(0, rank * NT - pc.t0);
-      const int jhi = min(V, rank * NT + NT - pc.t0);
-      Vr = jhi - jlo;
-      lo_site = site_start(jlo);
-      hi_site = site_start(jhi);
-      sbase = (pc.t0 + jlo - rank * NT) * S - lo_site;  // staged index of piece site li: sbase + li
-      x_first = (pc.x0 + lo_site + (j - jlo)) % N;
       fs = static_cast<const T*>(a.src.f) + d.off;
-      fd = static_cast<T*>(a.dst.f) + d.off;
     }
 
     // ---- load: coalesced global reads of all planes into the staging area, then registers
     if (active) {
-      int64_t x = x_first;
-      for (int li = lo_site + (j - jlo); li < hi_site; li += Vr) {
+      int64_t x = G.x_first;
+      for (int li = G.lo_site + (G.j - G.jlo); li < G.hi_site; li += G.Vr) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) stage[i * NT * S + sbase + li] = to_compute(fs[(int64_t)i * a.src.plane + x], k.scale);
-        x += Vr;
-        while (x >= N) x -= N;
+        for (int i = 0; i < Q; ++i)
+          stage[i * NT * S + G.sbase + li] = to_compute(fs[(int64_t)i * a.src.plane + x], k.scale);
+        x += G.Vr;
+        while (x >= G.N) x -= G.N;
       }
     }
     __syncthreads();
@@ -565,7 +584,7 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
 #pragma unroll
       for (int i = 0; i < Q; ++i)
 #pragma unroll
-        for (int s = 0; s < S; ++s) f[i][s] = (s < S - 1 || full) ? stage[i * NT * S + sbase + start + s] : CT(0);
+        for (int s = 0; s < S; ++s) f[i][s] = (s < S - 1 || full) ? stage[i * NT * S + G.sbase + start + s] : CT(0);
     }
     // block-uniform: does a piece of this bundle span both blocks (then this block
     // has one thread with lrem and one with rrem, possibly the same thread)
@@ -573,7 +592,7 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
     if constexpr (CL == 2) {
       span = __syncthreads_or(lrem || rrem);
       // block-uniform: the bundle holds a lattice as two halves (one per block)
-      halves = __syncthreads_or(active && pc.halo > 0);
+      halves = __syncthreads_or(active && a.pieces[pidx].halo > 0);
     } else {
       __syncthreads();
     }
@@ -610,24 +629,30 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
     __syncthreads();
 
     // ---- store: registers into the staging area, then coalesced global writes of all planes
+    Piece pc{};
     if (active) {
+      pc = a.pieces[pidx];  // read anew (after the barriers of the steps)
+      G = piece_geom<S>(pc, a.runs[pc.run].N, g, rank, NT);
 #pragma unroll
       for (int i = 0; i < Q; ++i)
 #pragma unroll
         for (int s = 0; s < S; ++s)
-          if (s < S - 1 || full) stage[i * NT * S + sbase + start + s] = f[i][s];
+          if (s < S - 1 || G.full) stage[i * NT * S + G.sbase + G.start + s] = f[i][s];
     }
     __syncthreads();
     if (active) {
-      int64_t x = x_first;
-      for (int li = lo_site + (j - jlo); li < hi_site; li += Vr) {
+      const RunDesc& d = a.runs[pc.run];
+      const CT inv_scale = load_coef<CT, Q>(d).inv_scale;
+      T* const fd = static_cast<T*>(a.dst.f) + d.off;
+      int64_t x = G.x_first;
+      for (int li = G.lo_site + (G.j - G.jlo); li < G.hi_site; li += G.Vr) {
         if (li >= pc.st_lo && li < pc.st_hi) {
 #pragma unroll
           for (int i = 0; i < Q; ++i)
-            from_compute(stage[i * NT * S + sbase + li], k.inv_scale, fd + (int64_t)i * a.dst.plane + x);
+            from_compute(stage[i * NT * S + G.sbase + li], inv_scale, fd + (int64_t)i * a.dst.plane + x);
         }
-        x += Vr;
-        while (x >= N) x -= N;
+        x += G.Vr;
+        while (x >= G.N) x -= G.N;
       }
     }
     __syncthreads();
