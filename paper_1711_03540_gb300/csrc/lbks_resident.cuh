@@ -225,8 +225,9 @@ __device__ __forceinline__ void push_edge_left(const CT (&f)[Q][SF], const CT (&
       constexpr int base = kk * (kk - 1) / 2;
 #pragma unroll
       for (int j = 0; j < kk; ++j) {
-        // phase B takes rho a_i of the -c plane from the +c plane before it (a_i is even in c)
-        const CT v = post_collision(k.r, f[i][j], rho[j], rho2[j], k.b[i], mul_rn(rho[j], k.a[i - 1]));
+        // phase B takes rho a_i of the -c plane from the +c plane before it (a_i is even in
+        // c) and b_i as minus that plane's (b_i is odd in c, exactly)
+        const CT v = post_collision(k.r, f[i][j], rho[j], rho2[j], -k.b[i - 1], mul_rn(rho[j], k.a[i - 1]));
         st_async(col + (uint32_t)((base + j) * ntx * sizeof(CT)), v, mbar);
       }
     }
@@ -319,7 +320,9 @@ __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>&
         } else {
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
+            // b_i of the -c plane is exactly minus the +c plane's (B_i = J w1_i, w1 odd in
+            // c), taken with the FMA's negation so that it needs no register of its own
+            const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], -k.b[i - 1], tt[s]);
             acc[s] = add_rn(acc[s], -v);
             if (s >= kk) f[i][s - kk] = v;
             else xl[(base + s) * NTX + t] = v;

@@ -58,6 +58,24 @@ def test_params_match_oracle(lb, Q, alpha, beta, tau, dmv):
     assert abs(B.sum()) < 1e-15
 
 
+@pytest.mark.parametrize("Q", [5, 7])
+@pytest.mark.parametrize("dmv", [0, 1, 2, 3])
+def test_params_exact_pair_symmetry(lb, Q, dmv):
+    """A_i is even and B_i odd in c_i exactly (bitwise, also after division by tau and
+    rounding to FP32): the resident kernels take rho a_i and b_i of each -c plane from
+    the +c plane before it."""
+    import numpy as np
+
+    for dx, dt, tau in [(0.1, 1e-4, 1.51), (0.2, 5e-5, 1.0), (0.0245, 5e-6, 3.0), (0.4, 2e-4, 2.7)]:
+        A, B, _ = lb.lb_ks_params(Q, dx, dt, tau, dmv)
+        for p in range(1, (Q - 1) // 2 + 1):
+            assert A[2 * p] == A[2 * p - 1]
+            assert B[2 * p] == -B[2 * p - 1]
+            a, b = A / tau, B / tau
+            assert a[2 * p] == a[2 * p - 1] and b[2 * p] == -b[2 * p - 1]
+            assert np.float32(b[2 * p]) == -np.float32(b[2 * p - 1])
+
+
 def test_params_reject_invalid(lb):
     for args in [(6, 0.1, 1e-4, 1.0), (7, 0.0, 1e-4, 1.0), (7, 0.1, -1.0, 1.0), (7, 0.1, 1e-4, 0.5),
                  (7, 0.1, 1e-4, math.nan)]:
