@@ -9,7 +9,6 @@
 #include <mutex>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/lb_ks.h"
@@ -91,6 +90,7 @@ struct lb_ks {
   double* d_energy = nullptr;
   double* d_delta = nullptr;
   int* d_flags = nullptr;
+  int* d_bad_run = nullptr;  // init: the first run whose rho0 holds a non-finite value (nruns: none)
   // resident kernel: up to three lanes, whole lattices first (one block, then cluster
   // pairs), segmented lattices last
   int S = 0, NT = 0, kmax = 0, kseg = 0, nlanes = 0;
@@ -923,122 +923,43 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   h->N.assign(N, N + nruns);
   h->total_sites = total;
 
-  // rho0 is read in place when the host can read it; a device pointer is copied down
-  // once.  Validation, mass, mean and the FP16 scale per run.
-  std::vector<double> r0_copy;
-  const double* r0 = rho0;
-  {
-    cudaPointerAttributes pa{};
-    if (cudaPointerGetAttributes(&pa, rho0) == cudaSuccess && pa.type == cudaMemoryTypeDevice) {
-      r0_copy.resize((size_t)total);
-      ce = cudaMemcpy(r0_copy.data(), rho0, sizeof(double) * (size_t)total, cudaMemcpyDeviceToHost);
-      if (ce != cudaSuccess) {
-        cudaGetLastError();
-        return bail(fail(h, LB_KS_EINVAL, std::string("cannot read rho0: ") + cudaGetErrorString(ce)));
-      }
-      r0 = r0_copy.data();
-    } else {
-      cudaGetLastError();
-    }
-  }
+  // Per run on the host: the coefficients and the arena layout.  The statistics of rho0
+  // (finiteness, mass M0, mean rhobar, FP16 scale) are computed on the device after the
+  // upload below, while the host plans.
   h->rho_off.resize(nruns + 1);
   h->rho_off[0] = 0;
   for (int32_t r = 0; r < nruns; ++r) h->rho_off[r + 1] = h->rho_off[r] + N[r];
   h->runs_h.resize(nruns);
-  h->mass0_h.resize(nruns);
-  std::vector<int> run_err(nruns, 0);  // 1: coefficients not finite, 2: rho0 not finite
-  // everything of a run but its offset in the arena
-  auto per_run = [&](int32_t rb, int32_t re) {
-    for (int32_t r = rb; r < re; ++r) {
-      RunDesc& d = h->runs_h[r];
-      std::memset(&d, 0, sizeof(d));
-      double A[7], B[7];
-      // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
-      const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
-      if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK) {
-        run_err[r] = 1;
-        continue;
-      }
-      // four interleaved partial sums (a single dependent chain is latency-bound),
-      // in a fixed order, so the result does not depend on the threads used
-      double m4[4] = {0.0, 0.0, 0.0, 0.0};
-      bool finite = true;
-      const double* rr = r0 + h->rho_off[r];
-      int64_t x = 0;
-      for (; x + 4 <= N[r]; x += 4) {
-        for (int q = 0; q < 4; ++q) {
-          finite &= std::isfinite(rr[x + q]);
-          m4[q] += rr[x + q];
-        }
-      }
-      for (; x < N[r]; ++x) {
-        finite &= std::isfinite(rr[x]);
-        m4[0] += rr[x];
-      }
-      const double mass = (m4[0] + m4[1]) + (m4[2] + m4[3]);
-      if (!finite) {
-        run_err[r] = 2;
-        continue;
-      }
-      h->mass0_h[r] = mass;
-      const double rhobar = o.precision == kF64 ? 0.0 : mass / (double)N[r];
-      double gmax = 0.0;
-      if (o.precision == kF16S) {
-        for (int64_t x = 0; x < N[r]; ++x)
-          for (int i = 0; i < scheme; ++i) {
-            double v = A[i] * rr[x] + B[i] * rr[x] * rr[x] - (i == 0 ? rhobar : 0.0);
-            gmax = std::max(gmax, std::fabs(v));
-          }
-      }
-      const double scale = (o.precision == kF16S && gmax > 0.0) ? gmax : 1.0;
-      const double w = 1.0 / tau[r];
-      d.N = N[r];
-      d.reservoir = reservoir ? 1 : 0;
-      d.rho_left = reservoir ? rho_left[r] : 0.0;
-      d.rho_right = reservoir ? rho_right[r] : 0.0;
-      for (int i = 0; i < scheme; ++i) {
-        d.A[i] = A[i];
-        d.B[i] = B[i];
-        d.a[i] = A[i] * w;
-        d.b[i] = B[i] * w;
-        d.af[i] = (float)d.a[i];
-        d.bf[i] = (float)d.b[i];
-      }
-      d.r = 1.0 - w;
-      d.rhobar = rhobar;
-      d.scale = scale;
-      d.inv_scale = 1.0 / scale;
-      d.rf = (float)d.r;
-      d.rhobarf = (float)d.rhobar;
-      d.scalef = (float)scale;
-      d.inv_scalef = (float)(1.0 / scale);
-    }
-  };
-  // Large batches: contiguous groups of runs of about equal sites (at least 2^18), one
-  // host thread each.
-  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
-  const int64_t nthreads = std::max<int64_t>(1, std::min<int64_t>({hw, 32, total >> 18, (int64_t)nruns}));
-  if (nthreads == 1) {
-    per_run(0, nruns);
-  } else {
-    std::vector<std::thread> pool;
-    int32_t rb = 0;
-    for (int64_t t = 0; t < nthreads && rb < nruns; ++t) {
-      const int64_t target = total * (t + 1) / nthreads;
-      int32_t re = rb + 1;
-      while (re < nruns && h->rho_off[re] < target) ++re;
-      if (t == nthreads - 1) re = nruns;
-      pool.emplace_back(per_run, rb, re);
-      rb = re;
-    }
-    for (std::thread& th : pool) th.join();
-  }
+  h->mass0_h.assign(nruns, 0.0);
   int64_t off = 0;
   for (int32_t r = 0; r < nruns; ++r) {
-    if (run_err[r] == 1) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
-    if (run_err[r] == 2) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": rho0 is not finite"));
+    RunDesc& d = h->runs_h[r];
+    std::memset(&d, 0, sizeof(d));
+    double A[7], B[7];
+    // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
+    const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
+    if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK)
+      return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
+    const double w = 1.0 / tau[r];
+    d.N = N[r];
+    d.reservoir = reservoir ? 1 : 0;
+    d.rho_left = reservoir ? rho_left[r] : 0.0;
+    d.rho_right = reservoir ? rho_right[r] : 0.0;
+    for (int i = 0; i < scheme; ++i) {
+      d.A[i] = A[i];
+      d.B[i] = B[i];
+      d.a[i] = A[i] * w;
+      d.b[i] = B[i] * w;
+      d.af[i] = (float)d.a[i];
+      d.bf[i] = (float)d.b[i];
+    }
+    d.r = 1.0 - w;
+    d.rf = (float)d.r;
+    d.rhobar = 0.0;  // rhobar and the FP16 scale: set on the device
+    d.scale = d.inv_scale = 1.0;
+    d.scalef = d.inv_scalef = 1.0f;
     const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
-    h->runs_h[r].off = off + ghost;
+    d.off = off + ghost;
     off += align_up(N[r] + 2 * ghost, kAlign);
   }
   h->plane = std::max<int64_t>(off, kAlign);
@@ -1079,13 +1000,13 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   if ((rc = dalloc(h, &h->d_energy, nruns))) return bail(rc);
   if ((rc = dalloc(h, &h->d_delta, nruns))) return bail(rc);
   if ((rc = dalloc(h, &h->d_flags, 1))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_bad_run, 1))) return bail(rc);
   auto up = [&](void* dst, const void* src, size_t bytes) { return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice); };
   if ((ce = up(h->d_runs, h->runs_h.data(), sizeof(RunDesc) * nruns)) != cudaSuccess ||
       (ce = up(h->d_plain_tiles, pt.data(), sizeof(Tile) * pt.size())) != cudaSuccess ||
       (ce = up(h->d_stream_tiles, st.data(), sizeof(Tile) * st.size())) != cudaSuccess ||
       (ce = up(h->d_stream_tile_begin, st_begin.data(), sizeof(int32_t) * st_begin.size())) != cudaSuccess ||
       (ce = up(h->d_rho_off, h->rho_off.data(), sizeof(int64_t) * h->rho_off.size())) != cudaSuccess ||
-      (ce = up(h->d_mass0, h->mass0_h.data(), sizeof(double) * nruns)) != cudaSuccess ||
       (ce = cudaMemset(h->d_flags, 0, sizeof(int))) != cudaSuccess)
     return bail(cuda_fail(h, ce, "upload"));
   // rho0 goes up on the handle's stream while the host plans below; the init kernels
@@ -1105,6 +1026,17 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
       (ce = cudaEventCreateWithFlags(&staged.ev, cudaEventDisableTiming)) != cudaSuccess ||
       (ce = cudaEventRecord(staged.ev, h->stream)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "upload rho0"));
+  // rho0's statistics on the device, read back after planning (once the event after
+  // them has completed: the read-back copies are not in the handle's stream)
+  CopyWait stats;
+  const int no_bad = nruns;
+  if ((ce = cudaMemcpyAsync(h->d_bad_run, &no_bad, sizeof(int), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (ce = launch_init_stats(scheme, h->prec, nruns, h->d_stage, h->d_rho_off, h->d_runs, h->d_stream_tiles,
+                              h->n_stream_tiles, h->d_stream_tile_begin, h->d_partials, h->d_mass0, h->d_bad_run,
+                              h->stream)) != cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&stats.ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventRecord(stats.ev, h->stream)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "rho0 statistics"));
 
   // Kernel family.
   int kern = o.kernel;
@@ -1161,6 +1093,14 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     }
   }
   if ((ce = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, ce, "init sync"));
+  // rho0's statistics, computed on the device while the host planned
+  int bad_run = nruns;
+  if ((ce = cudaEventSynchronize(stats.ev)) != cudaSuccess ||
+      (ce = cudaMemcpy(&bad_run, h->d_bad_run, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (ce = cudaMemcpy(h->runs_h.data(), h->d_runs, sizeof(RunDesc) * nruns, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (ce = cudaMemcpy(h->mass0_h.data(), h->d_mass0, sizeof(double) * nruns, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "read rho0 statistics"));
+  if (bad_run < nruns) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(bad_run) + ": rho0 is not finite"));
   warn_if_linearly_unstable(h, L, dt, tau);
   *out = h;
   return LB_KS_OK;

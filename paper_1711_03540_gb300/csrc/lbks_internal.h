@@ -81,6 +81,12 @@ cudaError_t launch_stream_step(int Q, int storage, Arena src, Arena dst, const R
 // writes f^eq(rho_bc) into the reservoir nodes of dst and nothing else (initial state).
 cudaError_t launch_reservoir_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
                                   const Tile* tiles, int ntiles, int reset_only, cudaStream_t s);
+// Initial statistics of rho0 (FP64, staged on the device; tiles cover [0, N) of each run):
+// mass0 per run, rhobar (and for F16S the storage scale) written into runs, and the first
+// run holding a non-finite value atomically min-ed into bad_run (scratch: 2 doubles per tile).
+cudaError_t launch_init_stats(int Q, int storage, int nruns, const double* rho0, const int64_t* rho_off,
+                              RunDesc* runs, const Tile* tiles, int ntiles, const int32_t* tile_begin,
+                              double* partials, double* mass0, int* bad_run, cudaStream_t s);
 // Guard: per-tile FP64 partial sums of rho and rho^2 (scratch: 2 doubles per tile),
 // then per-run totals, non-finite flag, and (if recentre) g_0 += (M0 - M)/N.
 cudaError_t launch_mass_partials(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles,

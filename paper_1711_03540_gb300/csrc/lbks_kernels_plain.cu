@@ -276,6 +276,119 @@ __global__ void __launch_bounds__(kRecentreThreads) recentre_kernel(Arena f, con
   if (threadIdx.x == 0) add_carry<ST>(base, carry, scale, inv);
 }
 
+// Initial statistics of rho0 (staged in FP64 on the device), pass 1: per tile the FP64
+// sum of rho0 and the number of non-finite values, in the fixed order of the guard's
+// partial sums (thread-strided, warp tree, warps in order).
+__global__ void __launch_bounds__(kPlainThreads) init_stats_partials_kernel(const double* __restrict__ rho0,
+                                                                           const int64_t* __restrict__ rho_off,
+                                                                           const Tile* __restrict__ tiles,
+                                                                           double* __restrict__ partials) {
+  const Tile tl = tiles[blockIdx.x];
+  const double* r = rho0 + rho_off[tl.run] + tl.x0;
+  double m = 0.0, bad = 0.0;
+  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+    const double v = r[k];
+    if (isfinite(v)) m += v;
+    else bad += 1.0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  __shared__ double sm[2][kPlainThreads / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sm[0][w] = m; sm[1][w] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mm = 0.0, bb = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { mm += sm[0][i]; bb += sm[1][i]; }
+    partials[2 * blockIdx.x] = mm;
+    partials[2 * blockIdx.x + 1] = bb;
+  }
+}
+
+// Pass 2: one warp per run sums its tiles' partials in a fixed order: the initial mass
+// M0 (the guard's re-centring target), the mean rhobar = M0 / N that the deviation
+// form stores g_0 against (0 for FP64 storage), and the first run with a non-finite
+// value (atomicMin into bad_run).
+__global__ void init_stats_finalize_kernel(int nruns, int storage, const int32_t* __restrict__ tile_begin,
+                                           const double* __restrict__ partials, RunDesc* __restrict__ runs,
+                                           double* __restrict__ mass0, int* __restrict__ bad_run) {
+  const int run = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (run >= nruns) return;
+  double m = 0.0, bad = 0.0;
+  for (int t = tile_begin[run] + lane; t < tile_begin[run + 1]; t += 32) {
+    m += partials[2 * t];
+    bad += partials[2 * t + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (lane == 0) {
+    mass0[run] = m;
+    if (bad > 0.0) atomicMin(bad_run, run);
+    const double rhobar = storage == kF64 ? 0.0 : m / static_cast<double>(runs[run].N);
+    runs[run].rhobar = rhobar;
+    runs[run].rhobarf = (float)rhobar;
+  }
+}
+
+// Scaled FP16 storage, pass 3: per tile the largest |g_i| of the initial state,
+// g_i = A_i rho + B_i rho^2 (minus rhobar for i = 0), over sites and planes.
+template <int Q>
+__global__ void __launch_bounds__(kPlainThreads) init_scale_partials_kernel(const double* __restrict__ rho0,
+                                                                           const int64_t* __restrict__ rho_off,
+                                                                           const RunDesc* __restrict__ runs,
+                                                                           const Tile* __restrict__ tiles,
+                                                                           double* __restrict__ partials) {
+  const Tile tl = tiles[blockIdx.x];
+  const RunDesc& d = runs[tl.run];
+  const double* r = rho0 + rho_off[tl.run] + tl.x0;
+  double g = 0.0;
+  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+    const double v = r[k], v2 = __dmul_rn(v, v);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double gi = __fma_rn(d.B[i], v2, __dmul_rn(d.A[i], v));
+      if (i == 0) gi = __dsub_rn(gi, d.rhobar);
+      g = fmax(g, fabs(gi));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+  __shared__ double sm[kPlainThreads / 32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gg = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) gg = fmax(gg, sm[i]);
+    partials[blockIdx.x] = gg;
+  }
+}
+
+// Pass 4: per run, the FP16 storage scale (the largest |g_i|, or 1 for a zero state).
+__global__ void init_scale_finalize_kernel(int nruns, const int32_t* __restrict__ tile_begin,
+                                           const double* __restrict__ partials, RunDesc* __restrict__ runs) {
+  const int run = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (run >= nruns) return;
+  double g = 0.0;
+  for (int t = tile_begin[run] + lane; t < tile_begin[run + 1]; t += 32) g = fmax(g, partials[t]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+  if (lane == 0) {
+    const double scale = g > 0.0 ? g : 1.0;
+    runs[run].scale = scale;
+    runs[run].inv_scale = 1.0 / scale;
+    runs[run].scalef = (float)scale;
+    runs[run].inv_scalef = (float)(1.0 / scale);
+  }
+}
+
 // FMA-pipe micro-benchmark: independent chains of fused multiply-adds.
 template <typename T>
 __global__ void fma_peak_kernel(T* out, int iters, T seed) {
@@ -352,6 +465,22 @@ cudaError_t launch_mass_partials(int Q, int storage, Arena src, const RunDesc* r
     return cudaGetLastError();
   }
   LBKS_DISPATCH_Q_ST(Q, storage, (mass_partials_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, runs, tiles, partials)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_stats(int Q, int storage, int nruns, const double* rho0, const int64_t* rho_off,
+                              RunDesc* runs, const Tile* tiles, int ntiles, const int32_t* tile_begin,
+                              double* partials, double* mass0, int* bad_run, cudaStream_t s) {
+  if (ntiles == 0 || nruns == 0) return cudaSuccess;
+  const int fin_blocks = (nruns * 32 + 127) / 128;
+  init_stats_partials_kernel<<<ntiles, kPlainThreads, 0, s>>>(rho0, rho_off, tiles, partials);
+  init_stats_finalize_kernel<<<fin_blocks, 128, 0, s>>>(nruns, storage, tile_begin, partials, runs, mass0, bad_run);
+  if (storage == kF16S) {
+    if (Q == 5) init_scale_partials_kernel<5><<<ntiles, kPlainThreads, 0, s>>>(rho0, rho_off, runs, tiles, partials);
+    else if (Q == 7) init_scale_partials_kernel<7><<<ntiles, kPlainThreads, 0, s>>>(rho0, rho_off, runs, tiles, partials);
+    else return cudaErrorInvalidValue;
+    init_scale_finalize_kernel<<<fin_blocks, 128, 0, s>>>(nruns, tile_begin, partials, runs);
+  }
   return cudaGetLastError();
 }
 

@@ -326,3 +326,18 @@ def test_init_warns_about_linearly_unstable_runs(lb):
         assert lb.lb_ks_last_error(h) == "no error"
     finally:
         lb.lb_ks_free(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_nonfinite_rho0_is_einval_naming_the_first_run(lb, prec):
+    """rho0's finiteness is checked on the device (with its mass, mean and FP16 scale):
+    a NaN in run 2 and an Inf in run 3 give EINVAL naming run 2, and no handle."""
+    Ns = np.array([64, 100, 80, 90], dtype=np.int64)
+    r0 = 0.01 * np.random.default_rng(9).standard_normal(int(Ns.sum()))
+    r0[64 + 100 + 5] = np.nan
+    r0[64 + 100 + 80 + 3] = np.inf
+    with pytest.raises(lb.LbKsError) as e:
+        lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(4, 1e-4), np.full(4, 2.0), r0,
+                            lb.lb_ks_default_opts(precision=prec, kernel=lb.KERNEL_RESIDENT))
+    assert e.value.code == -1
+    assert "run 2: rho0 is not finite" in lb.lb_ks_last_error(None)
