@@ -12,8 +12,9 @@ constexpr int kMaxQ = 7;
 // Storage precisions (same values as LB_KS_F64 / LB_KS_F32 / LB_KS_F16S).
 enum Storage : int { kF64 = 0, kF32 = 1, kF16S = 2 };
 
-// Per-run constants, computed in FP64 on the host (lbks_params.cpp) and
-// uploaded once.  The step of Eq. LB_equation_ordinary is evaluated as
+// Per-run constants, computed in FP64 on the host (lbks_params.cpp) and uploaded
+// once; rhobar and the FP16 scale, which depend on rho0, are filled in on the device
+// (launch_init_stats).  The step of Eq. LB_equation_ordinary is evaluated as
 //     rho  = rhobar + sum_i g_i                 (g_i = f_i - w0_i rhobar, the stored deviation)
 //     g*_i = r g_i + rho a_i + rho^2 b_i        (i >= 1)
 //     g*_0 = sum_i g_i - sum_{i>=1} g*_i        (mass conservation of the collision)
