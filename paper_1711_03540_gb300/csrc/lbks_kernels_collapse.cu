@@ -166,43 +166,55 @@ __global__ void __launch_bounds__(kCRThreads, 1) collapse_resident_kernel(const 
 
     CT e[S + 2 * C];
     CollapseCoef<CT, C> k;
+    // where the thread's sites sit (computed before the load and again, from the piece
+    // read anew, before the store, so that none of it is held through the steps)
+    struct Geom {
+      int64_t N, x_first;
+      int j, V, start, sbase;
+      bool full;
+    };
+    auto geom = [&](const Piece& pc, int64_t N) {
+      Geom G;
+      G.N = N;
+      G.j = t - pc.t0;
+      G.V = pc.nthr;
+      const int mfull = pc.n - G.V * (S - 1);  // threads holding S sites; the rest hold S-1
+      G.full = G.j < mfull;
+      G.start = G.full ? G.j * S : mfull * S + (G.j - mfull) * (S - 1);
+      G.x_first = (pc.x0 + G.j) % N;
+      G.sbase = pc.t0 * S;
+      return G;
+    };
     bool full = true;
-    int j = 0, V = 1, start = 0, left = t, right = t;
-    Piece pc{};
-    int64_t N = 1, x_first = 0;
+    int left = t, right = t;
+    Geom G{};
+    int n = 0;
     const T* fs = nullptr;
-    T* fd = nullptr;
     if (active) {
-      pc = a.pieces[pidx];
+      const Piece pc = a.pieces[pidx];
       const RunDesc& d = a.runs[pc.run];
       k = load_collapse_coef<CT, C>(d);
-      N = d.N;
-      j = t - pc.t0;
-      V = pc.nthr;
-      const int mfull = pc.n - V * (S - 1);  // threads holding S sites; the rest hold S-1
-      full = j < mfull;
-      start = full ? j * S : mfull * S + (j - mfull) * (S - 1);
-      left = pc.t0 + (j == 0 ? V - 1 : j - 1);
-      right = pc.t0 + (j == V - 1 ? 0 : j + 1);
-      x_first = (pc.x0 + j) % N;
+      G = geom(pc, d.N);
+      full = G.full;
+      n = pc.n;
+      left = pc.t0 + (G.j == 0 ? G.V - 1 : G.j - 1);
+      right = pc.t0 + (G.j == G.V - 1 ? 0 : G.j + 1);
       fs = static_cast<const T*>(a.src.f) + d.off;
-      fd = static_cast<T*>(a.dst.f) + d.off;
     }
-    const int sbase = pc.t0 * S;
 
     // ---- load: coalesced global reads into the staging area, then registers
     if (active) {
-      int64_t x = x_first;
-      for (int li = j; li < pc.n; li += V) {
-        stage[sbase + li] = static_cast<CT>(fs[x]);
-        x += V;
-        while (x >= N) x -= N;
+      int64_t x = G.x_first;
+      for (int li = G.j; li < n; li += G.V) {
+        stage[G.sbase + li] = static_cast<CT>(fs[x]);
+        x += G.V;
+        while (x >= G.N) x -= G.N;
       }
     }
     __syncthreads();
     if (active) {
 #pragma unroll
-      for (int s = 0; s < S; ++s) e[C + s] = (s < S - 1 || full) ? stage[sbase + start + s] : CT(0);
+      for (int s = 0; s < S; ++s) e[C + s] = (s < S - 1 || full) ? stage[G.sbase + G.start + s] : CT(0);
     }
     __syncthreads();
 
@@ -243,18 +255,22 @@ __global__ void __launch_bounds__(kCRThreads, 1) collapse_resident_kernel(const 
     }
 
     // ---- store: registers into the staging area, then coalesced global writes
+    Piece pc{};
     if (active) {
+      pc = a.pieces[pidx];  // read anew (after the barriers of the steps)
+      G = geom(pc, a.runs[pc.run].N);
 #pragma unroll
       for (int s = 0; s < S; ++s)
-        if (s < S - 1 || full) stage[sbase + start + s] = e[C + s];
+        if (s < S - 1 || G.full) stage[G.sbase + G.start + s] = e[C + s];
     }
     __syncthreads();
     if (active) {
-      int64_t x = x_first;
-      for (int li = j; li < pc.n; li += V) {
-        if (li >= pc.st_lo && li < pc.st_hi) fd[x] = static_cast<T>(stage[sbase + li]);
-        x += V;
-        while (x >= N) x -= N;
+      T* const fd = static_cast<T*>(a.dst.f) + a.runs[pc.run].off;
+      int64_t x = G.x_first;
+      for (int li = G.j; li < pc.n; li += G.V) {
+        if (li >= pc.st_lo && li < pc.st_hi) fd[x] = static_cast<T>(stage[G.sbase + li]);
+        x += G.V;
+        while (x >= G.N) x -= G.N;
       }
     }
     __syncthreads();
