@@ -1062,7 +1062,9 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     return bail(cuda_fail(h, ce, "stream kernel setup"));
   if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "create capture stream"));
-  if (kern == LB_KS_KERNEL_RESIDENT || h->collapse_resident) {
+  // streams and events for concurrent lanes, when the plan has several (or the tuner
+  // may choose one that does)
+  if ((kern == LB_KS_KERNEL_RESIDENT || h->collapse_resident) && (o.autotune || h->nlanes > 1)) {
     for (int l = 0; l < 2 && ce == cudaSuccess; ++l)
       if ((ce = cudaStreamCreateWithFlags(&h->side_stream[l], cudaStreamNonBlocking)) == cudaSuccess)
         ce = cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming);
@@ -1070,6 +1072,7 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "create lane stream"));
     if (o.autotune && (rc = autotune_resident(h)) != LB_KS_OK) return bail(rc);
   }
+  if (h->nlanes > 1 && !h->ev_fork) return bail(fail(h, LB_KS_ECUDA, "internal: lanes without their streams"));
 
   if (kern == LB_KS_KERNEL_COLLAPSE) {
     // rho - rhobar in both arenas (reservoir ends and ghosts keep their values in both)
