@@ -156,6 +156,20 @@ def test_cluster_halves_bitwise_with_launch_lengths(lb, recentre):
     np.testing.assert_array_equal(halves, plain)
 
 
+def test_cluster_halves_f16s_one_step_per_launch_equals_stream(lb):
+    """Scaled FP16 storage rounds at every launch edge; with one step per launch the
+    halves (segments with halos, loaded and stored every step) round where the
+    streaming kernel does."""
+    Ns = np.array([2500, 3001, 300], dtype=np.int64)
+    r0, taus = _inputs(Ns, 84)
+    r0 = 0.01 * r0
+    a, _ = run_gpu(lb, 7, Ns, r0, 40, taus, kernel=2, precision=2)
+    b, d = run_gpu(lb, 7, Ns, r0, 40, taus, kernel=3, precision=2, sites_per_thread=8, threads_per_block=256,
+                   cluster_size=2, steps_per_launch=1)
+    assert sum(ln["halved_lattices"] for ln in d["lanes"]) == 2
+    np.testing.assert_array_equal(a, b)
+
+
 def test_cluster_halves_checkpoint(lb):
     """A checkpoint taken between launches of a run with halves restores it bitwise."""
     Ns = np.array(HALVES_NS[:7], dtype=np.int64)
