@@ -174,6 +174,52 @@ __device__ __forceinline__ void site_sums(const typename StorageType<ST>::type* 
   }
 }
 
+// FP32 storage, tile start 16-byte aligned: thread k sums sites 4k .. 4k+3 of the tile,
+// one 16-byte load per plane (the per-site arithmetic of site_sums, sites in order).
+template <int Q>
+__device__ __forceinline__ void site_sums_vec4(const float* f, int64_t plane, const RunDesc& d, int k, int len,
+                                               double& m, double& e) {
+  const float rb_hi = (float)d.rhobar, rb_lo = (float)(d.rhobar - (double)rb_hi);
+  float mh = 0.f, ml = 0.f, eh = 0.f, el = 0.f;
+  const int x = 4 * k;
+  if (x < len) {
+    float v[Q][4];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float* p = f + (int64_t)i * plane + x;
+      if (x + 4 <= len) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[i][0] = q.x; v[i][1] = q.y; v[i][2] = q.z; v[i][3] = q.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[i][u] = x + u < len ? p[u] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (x + u >= len) break;
+      float hi = rb_hi, lo = rb_lo, t, te;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        two_sum(hi, v[i][u], t, te);
+        hi = t;
+        lo = __fadd_rn(lo, te);
+      }
+      two_sum(hi, lo, hi, lo);  // renormalise
+      two_sum(mh, hi, t, te);
+      mh = t;
+      ml = __fadd_rn(ml, __fadd_rn(te, lo));
+      const float p2 = __fmul_rn(hi, hi);
+      const float pe = __fmaf_rn(hi, hi, -p2);  // exact low part of hi^2
+      two_sum(eh, p2, t, te);
+      eh = t;
+      el = __fadd_rn(el, __fadd_rn(te, __fmaf_rn(2.f * hi, lo, pe)));
+    }
+  }
+  m = (double)mh + (double)ml;
+  e = (double)eh + (double)el;
+}
+
 // Guard, pass 1: FP64 sums of rho and rho^2 over one tile (fixed-order tree).
 template <int Q, int ST>
 __global__ void __launch_bounds__(kPlainThreads) mass_partials_kernel(Arena src, const RunDesc* __restrict__ runs,
@@ -183,7 +229,11 @@ __global__ void __launch_bounds__(kPlainThreads) mass_partials_kernel(Arena src,
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
   double m, e;
-  site_sums<Q, ST>(static_cast<const T*>(src.f) + d.off + tl.x0, src.plane, d, threadIdx.x, tl.len, blockDim.x, m, e);
+  const T* const base = static_cast<const T*>(src.f) + d.off + tl.x0;
+  if (ST == kF32 && Q > 1 && ((d.off + tl.x0) & 3) == 0 && (src.plane & 3) == 0 && tl.len <= 4 * (int)blockDim.x)
+    site_sums_vec4<Q>(reinterpret_cast<const float*>(base), src.plane, d, threadIdx.x, tl.len, m, e);
+  else
+    site_sums<Q, ST>(base, src.plane, d, threadIdx.x, tl.len, blockDim.x, m, e);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     m += __shfl_xor_sync(0xffffffffu, m, o);
@@ -269,7 +319,18 @@ __global__ void __launch_bounds__(kRecentreThreads) recentre_kernel(Arena f, con
   const int chunk = (tl.len + 31) / 32;
   const int k0 = threadIdx.x * chunk, k1 = min(tl.len, k0 + chunk);
   CT carry = CT(0);
-  for (int k = k0; k < k1; ++k) carry = add_carry<ST>(base + k, add_rn(dl, carry), scale, inv);
+  if (chunk <= 32) {
+    // the tile through shared memory: coalesced global loads and stores; lane L's chunk
+    // at padded rows (stride 33) so that the lanes' walks hit distinct banks
+    __shared__ T tile[32 * 33];
+    for (int k = threadIdx.x; k < tl.len; k += 32) tile[(k / chunk) * 33 + k % chunk] = base[k];
+    __syncwarp();
+    for (int k = k0; k < k1; ++k) carry = add_carry<ST>(tile + threadIdx.x * 33 + (k - k0), add_rn(dl, carry), scale, inv);
+    __syncwarp();
+    for (int k = threadIdx.x; k < tl.len; k += 32) base[k] = tile[(k / chunk) * 33 + k % chunk];
+  } else {
+    for (int k = k0; k < k1; ++k) carry = add_carry<ST>(base + k, add_rn(dl, carry), scale, inv);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) carry = add_rn(carry, __shfl_xor_sync(0xffffffffu, carry, o));
   __syncwarp();
