@@ -58,10 +58,10 @@ def parse():
                    help="collapse: the tau = 1 rho-only step, on the ensemble at tau = 1")
     p.add_argument("--precision", default="f32", choices=["f32", "f16s", "f64"])
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, e2e and CPU legs")
-    p.add_argument("--autotune", action="store_true",
-                   help="let the library time candidate plans at init and keep the fastest (the default is "
-                        "its fixed plan, whose launch sequence is deterministic and profiled)")
-    p.add_argument("--no-autotune", action="store_true", help="the fixed plan (the default)")
+    p.add_argument("--autotune", action="store_true", help="(the default) the library times candidate plans at "
+                                                            "init and keeps the fastest")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="the library's fixed plan (deterministic launch sequence, for profiling)")
     p.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2],
                    help="resident work group for whole lattices: 1 block, a 2-block cluster, 0 = auto")
     p.add_argument("--spt", type=int, default=0, help="resident sites per thread (0 = auto; for profiling a plan)")
@@ -251,8 +251,7 @@ def main():
     kern = {"resident": lb.KERNEL_RESIDENT, "stream": lb.KERNEL_STREAM, "plain": lb.KERNEL_PLAIN,
             "collapse": lb.KERNEL_COLLAPSE}[args.kernel]
     opts = lb.lb_ks_default_opts(precision=prec, recentre_every=0 if prec == lb.F64 else GUARD_EVERY, kernel=kern,
-                                 autotune=int(kern in (lb.KERNEL_RESIDENT, lb.KERNEL_COLLAPSE) and args.autotune
-                                              and not args.no_autotune),
+                                 autotune=int(kern in (lb.KERNEL_RESIDENT, lb.KERNEL_COLLAPSE) and not args.no_autotune),
                                  cluster_size=args.cluster, sites_per_thread=args.spt, threads_per_block=args.tpb,
                                  stream=stream)
     h = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, opts)
