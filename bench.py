@@ -358,8 +358,12 @@ def extras(lb, torch, wl, h_res, stream, line, local):
     Q = wl.scheme
     sites = wl.sites
     # Plain FP64 kernel on the same ensemble (the FP64 baseline), and the error of the
-    # FP32 resident run against it after the same number of steps.
-    nref = 1000
+    # FP32 resident run against it after the same number of steps: T = 1 (10^4 steps),
+    # the stated horizon of the FP32 tolerance.  Past it, FP32 rounding seeded into the
+    # growing KS modes (up to e^{T/4}) takes long lattices whose own modes sit in the
+    # nearly neutral band k < 0.13 beyond 1e-4 (tests/measure_ensemble_error.py: median
+    # run 6e-6, largest 1.7e-3 at T = 10).
+    nref = 10000
     o64 = lb.lb_ks_default_opts(precision=lb.F64, kernel=lb.KERNEL_PLAIN, stream=stream)
     h64 = lb.lb_ks_batch_init(Q, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, o64)
     o32 = lb.lb_ks_default_opts(precision=lb.F32, recentre_every=GUARD_EVERY, kernel=lb.KERNEL_RESIDENT, stream=stream)
@@ -387,7 +391,9 @@ def extras(lb, torch, wl, h_res, stream, line, local):
                           "steps_timed": nref - 100}
     line["vs_plain_fp64"] = line["value"] / v64 if line["n_gpus"] == 1 else None
     line["error"] = {"vs": "FP64 plain kernel (parity-tested against the oracle)", "lb_steps": nref,
+                     "T": nref * float(wl.dt[0]),
                      "rel_l2_global": float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64)),
+                     "rel_l2_median_run": float(np.median(per)),
                      "rel_l2_max_run": float(max(per)), "tolerance": 1e-4}
 
     # End to end through the C ABI with host buffers: per step, batch_init from
