@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -470,6 +471,29 @@ int upload_lane(lb_ks* h, Lane* L, const std::vector<Piece>& pieces, const Bins&
   return LB_KS_OK;
 }
 
+// The kernels' launch preparation (dynamic shared memory opt-in, resident blocks per SM
+// or clusters at once), done once per device, kind (0 resident, 1 collapse, 2 cluster
+// pairs), scheme, storage and tiling: the attribute set by it stays with the function.
+cudaError_t prepared(int kind, int Q, int prec, int S, int NT, int* out) {
+  static std::mutex mu;
+  static std::map<std::array<int, 6>, int> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const std::array<int, 6> key{dev, kind, Q, prec, S, NT};
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(key);
+  if (it == done.end()) {
+    int v = 0;
+    e = kind == 0 ? resident_prepare(Q, prec, S, NT, &v)
+                  : (kind == 1 ? collapse_resident_prepare(Q, prec, S, NT, &v) : resident_cluster_prepare(Q, prec, S, NT, &v));
+    if (e != cudaSuccess) return e;  // not kept: the caller clears the error and tries another tiling
+    it = done.emplace(key, v).first;
+  }
+  *out = it->second;
+  return cudaSuccess;
+}
+
 // Resident kernel plan.  Whole lattices (rings) run k_ring steps per launch; lattices
 // cut into segments run k_seg-step launches (their halo grows with the steps per
 // launch).  Rings of up to NT S sites run in single-block work groups; with cl = 2,
@@ -525,10 +549,10 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
     for (const Piece& p : rings) nhalves += p.halo > 0 ? 1 : 0;
     pack_blocks(segs, NT, &segbins);
     int bps = 0, max_clusters = 0;
-    cudaError_t e = col ? collapse_resident_prepare(h->Q, h->prec, S, NT, &bps) : resident_prepare(h->Q, h->prec, S, NT, &bps);
+    cudaError_t e = prepared(col ? 1 : 0, h->Q, h->prec, S, NT, &bps);
     if (e != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
     if (!pairs.used.empty()) {
-      e = resident_cluster_prepare(h->Q, h->prec, S, NT, &max_clusters);
+      e = prepared(2, h->Q, h->prec, S, NT, &max_clusters);
       if (e != cudaSuccess || max_clusters < 1) { cudaGetLastError(); continue; }
     }
     int dev = 0, sms = 0;

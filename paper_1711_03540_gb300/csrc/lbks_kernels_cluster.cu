@@ -26,8 +26,9 @@ cudaLaunchConfig_t cluster_config(int grid, int NT, cudaStream_t s, cudaLaunchAt
 template <int Q, int ST, int S>
 cudaError_t prepare_t(int NT, int* max_clusters) {
   if (NT > ResidentCfg<ST, S>::kMaxThreads || NT % 32 != 0) return cudaErrorInvalidValue;
-  const size_t smem = smem_bytes_t<Q, ST, S>(NT);
-  cudaError_t e = cudaFuncSetAttribute(resident_kernel<Q, ST, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the opt-in covers the largest block of this instantiation (see the single-block one)
+  cudaError_t e = cudaFuncSetAttribute(resident_kernel<Q, ST, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes_t<Q, ST, S>(ResidentCfg<ST, S>::kMaxThreads));
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr;
   const cudaLaunchConfig_t cfg = cluster_config<Q, ST, S>(1, NT, nullptr, &attr);

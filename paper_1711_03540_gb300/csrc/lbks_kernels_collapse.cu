@@ -298,9 +298,11 @@ size_t cr_smem_bytes(int NT) {
 
 template <int C, int ST, int S>
 cudaError_t cr_prepare_t(int NT, int* blocks_per_sm) {
+  // the opt-in covers the largest block (kCRThreads), so that preparing a smaller tiling
+  // later never lowers it under a larger one already prepared
   const size_t smem = cr_smem_bytes<C, ST, S>(NT);
   cudaError_t e = cudaFuncSetAttribute(collapse_resident_kernel<C, ST, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+                                       (int)cr_smem_bytes<C, ST, S>(kCRThreads));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, collapse_resident_kernel<C, ST, S>, NT, smem);
 }

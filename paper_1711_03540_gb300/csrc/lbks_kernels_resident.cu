@@ -9,8 +9,11 @@ namespace {
 template <int Q, int ST, int S>
 cudaError_t prepare_t(int NT, int* blocks_per_sm) {
   if (NT > ResidentCfg<ST, S>::kMaxThreads || NT % 32 != 0) return cudaErrorInvalidValue;
+  // the opt-in covers the largest block of this instantiation, so that preparing a
+  // smaller tiling later never lowers it under a larger one already prepared
   const size_t smem = smem_bytes_t<Q, ST, S>(NT);
-  cudaError_t e = cudaFuncSetAttribute(resident_kernel<Q, ST, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(resident_kernel<Q, ST, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes_t<Q, ST, S>(ResidentCfg<ST, S>::kMaxThreads));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, resident_kernel<Q, ST, S, 1>, NT, smem);
 }
