@@ -73,6 +73,10 @@ namespace {
 template <int ST, int S> struct ResidentCfg {
   // Upper bound of threads per block; sets the register budget per thread.
   static constexpr int kMaxThreads = (ST == kF64) ? 256 : (S <= 8 ? 512 : (S <= 12 ? 384 : 256));
+  // Row length of the exchange area: a column per thread of the largest block and two
+  // for the values the other block of a cluster pushes in.  A compile-time stride, so
+  // that every exchange access is a base address plus an immediate offset.
+  static constexpr int kXS = kMaxThreads + 2;
 };
 
 // Compile-time loop over I = B..E-1 (keeps every plane's speed a constant expression).
@@ -102,17 +106,17 @@ constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before a wait is g
 
 // Dynamic shared memory (elements): the staging area of the launch edges
 // [Q planes][NT threads x S sites], then the exchange area
-// [2 parities][2 directions][NX][NT + 2]: a column per thread for the values
-// leaving it, and two more (NT: right-moving, NT + 1: left-moving) for the values
-// the other block of a cluster pushes in, then the inbox of a lattice half
+// [2 parities][2 directions][NX][XS] (XS = ResidentCfg::kXS): a column per thread for
+// the values leaving it, and the last two (XS - 2: right-moving, XS - 1: left-moving)
+// for the values the other block of a cluster pushes in, then the inbox of a lattice half
 // [2 parities][2 sides][Q][c_max kPairStepsMax]: side 0 the other half's last halo
 // sites (this half's left halo), side 1 its first ones (the right halo).  Neither
 // overlaps the staging area, since the other block may write them while this block
 // is still staging.
 __host__ __device__ constexpr int exchange_rows(int Q) { return 4 * ((Q - 1) / 2) * ((Q - 1) / 2 + 1) / 2; }
 __host__ __device__ constexpr int halo_max(int Q) { return ((Q - 1) / 2) * kPairStepsMax; }
-__host__ __device__ constexpr size_t smem_elems(int Q, int S, int NT) {
-  return (size_t)Q * S * NT + (size_t)exchange_rows(Q) * (NT + 2) + (size_t)4 * Q * halo_max(Q);
+__host__ __device__ constexpr size_t smem_elems(int Q, int S, int NT, int XS) {
+  return (size_t)Q * S * NT + (size_t)exchange_rows(Q) * XS + (size_t)4 * Q * halo_max(Q);
 }
 
 // ---- thread block clusters (PTX ISA: barrier.cluster, mapa, ld.shared::cluster)
@@ -252,13 +256,13 @@ struct ClusterLink {
 // LINK: the bundle has a piece across the edge of a cluster pair, whose boundary
 // values go through the other block's shared memory; without it the loop is that of
 // a single block (no link code in the loop, so no registers or instructions spent on it).
-template <int Q, int S, bool LINK, typename CT>
+template <int Q, int S, int XS, bool LINK, typename CT>
 __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>& k, const int step0, const int ksteps,
                                                CT* const xbase, const int NT, const int t, const bool active,
                                                const bool full, const int lt, const int rt, ClusterLink& ln) {
   constexpr int C = cmax_of(Q);
   constexpr int NX = C * (C + 1) / 2;  // values leaving a thread per direction per step
-  const int NTX = NT + 2;
+  constexpr int NTX = XS;
   for (int step = step0; step < step0 + ksteps; ++step) {
     const int pb = step & 1;
     const int par = pb * 2 * NX * NTX;
@@ -286,12 +290,12 @@ __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>&
         // phase A's sums with the arithmetic of phase B (which computes them again
         // below), so that the transfer overlaps the rest of the step.
         if (ln.rrem) {
-          const uint32_t col = ln.peer_x + (uint32_t)((par + NT) * sizeof(CT));
+          const uint32_t col = ln.peer_x + (uint32_t)((par + XS - 2) * sizeof(CT));
           if (full) push_edge_right<Q, S>(f, rho, rho2, k, col, NTX, ln.peer_mbar + 8u * pb);
           else push_edge_right<Q, S - 1>(f, rho, rho2, k, col, NTX, ln.peer_mbar + 8u * pb);
         }
         if (ln.lrem)
-          push_edge_left<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)((par + NX * NTX + NT + 1) * sizeof(CT)), NTX,
+          push_edge_left<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)((par + NX * NTX + XS - 1) * sizeof(CT)), NTX,
                             ln.peer_mbar + 8u * pb);
       }
       // B. plane by plane: collide, write to the destination site's register or send.
@@ -483,9 +487,9 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
   constexpr int NX = C * (C + 1) / 2;  // values leaving a thread per direction per step
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NT = blockDim.x;
-  const int NTX = NT + 2;                              // exchange-area row length
+  constexpr int NTX = ResidentCfg<ST, S>::kXS;        // exchange-area row length
   CT* const stage = reinterpret_cast<CT*>(smem_raw);   // [Q][NT * S] at the launch edges
-  CT* const xbase = stage + Q * S * NT;                // [parity][R|L][NX][NT + 2]
+  CT* const xbase = stage + Q * S * NT;                // [parity][R|L][NX][NTX]
   CT* const inbox = xbase + exchange_rows(Q) * NTX;    // [parity][L|R halo][Q][c_max kPairStepsMax]
   __shared__ int s_bundle;
   __shared__ int s_half[3];                            // CL = 2: halo, own sites, threads of this block's half
@@ -566,8 +570,8 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       const int rrank = CL == 1 ? 0 : rg / NT;
       lrem = lrank != rank;
       rrem = rrank != rank;
-      lt = lrem ? NT : lg - lrank * NT;        // pushed-in columns for a neighbour in the other block
-      rt = rrem ? NT + 1 : rg - rrank * NT;
+      lt = lrem ? NTX - 2 : lg - lrank * NT;   // pushed-in columns for a neighbour in the other block
+      rt = rrem ? NTX - 1 : rg - rrank * NT;
       fs = static_cast<const T*>(a.src.f) + d.off;
     }
 
@@ -611,7 +615,7 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
         ln.rrem = rrem;
         ln.bad = s_bad != 0;
         ln.flags = a.flags;
-        resident_steps<Q, S, true>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
+        resident_steps<Q, S, NTX, true>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
         // every thread toggled the same parities; the next write follows the barriers
         // of the store phase below
         if (t == 0) s_ph = ln.ph;
@@ -619,15 +623,15 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       } else if (halves && a.kx > 0) {
         for (int s0 = 0; s0 < a.ksteps; s0 += a.kx) {
           const int kk = min(a.kx, a.ksteps - s0);
-          resident_steps<Q, S, false>(f, k, s0, kk, xbase, NT, t, active, full, lt, rt, ln);
+          resident_steps<Q, S, NTX, false>(f, k, s0, kk, xbase, NT, t, active, full, lt, rt, ln);
           if (s0 + kk < a.ksteps)
             halo_exchange<Q, S>(f, s_half, full, start, NT, t, stage, inbox, (s0 / a.kx) & 1);
         }
       } else {
-        resident_steps<Q, S, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
+        resident_steps<Q, S, NTX, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
       }
     } else {
-      resident_steps<Q, S, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
+      resident_steps<Q, S, NTX, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
     }
     __syncthreads();
 
@@ -665,7 +669,7 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
 template <int Q, int ST, int S>
 size_t smem_bytes_t(int NT) {
   using CT = typename StorageType<ST>::compute;
-  return sizeof(CT) * smem_elems(Q, S, NT);
+  return sizeof(CT) * smem_elems(Q, S, NT, ResidentCfg<ST, S>::kXS);
 }
 
 #define LBKS_RESIDENT_CASES(Q_, ST_, OP)                                              \
