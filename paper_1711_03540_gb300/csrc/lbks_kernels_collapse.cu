@@ -145,7 +145,10 @@ __global__ void __launch_bounds__(kCRThreads, 1) collapse_resident_kernel(const 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NT = blockDim.x;
   CT* const stage = reinterpret_cast<CT*>(smem_raw);  // [NT * S] at the launch edges
-  CT* const xbase = stage + NT * S;                    // [parity][R|L][C][NT]
+  // [parity][R|L][C][kCRThreads]: a compile-time row length, so that every exchange
+  // access is a base address plus an immediate offset
+  constexpr int XS = kCRThreads;
+  CT* const xbase = stage + NT * S;
   __shared__ int s_bundle;
   const int t = threadIdx.x;
 
@@ -219,21 +222,21 @@ __global__ void __launch_bounds__(kCRThreads, 1) collapse_resident_kernel(const 
     __syncthreads();
 
     for (int step = 0; step < a.ksteps; ++step) {
-      CT* const xr = xbase + (step & 1) * 2 * C * NT;  // a thread's last C values (read by its right neighbour)
-      CT* const xl = xr + C * NT;                       // its first C values (read by its left neighbour)
+      CT* const xr = xbase + (step & 1) * 2 * C * XS;  // a thread's last C values (read by its right neighbour)
+      CT* const xl = xr + C * XS;                       // its first C values (read by its left neighbour)
       if (active) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          xl[c * NT + t] = e[C + c];
-          xr[c * NT + t] = full ? e[S + c] : e[S - 1 + c];  // own sites end at C + S - 1 or C + S - 2
+          xl[c * XS + t] = e[C + c];
+          xr[c * XS + t] = full ? e[S + c] : e[S - 1 + c];  // own sites end at C + S - 1 or C + S - 2
         }
       }
       __syncthreads();
       if (active) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          e[c] = xr[c * NT + left];
-          const CT v = xl[c * NT + right];
+          e[c] = xr[c * XS + left];
+          const CT v = xl[c * XS + right];
           if (full) e[C + S + c] = v;
           else e[C + S - 1 + c] = v;
         }
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(kCRThreads, 1) collapse_resident_kernel(const 
 template <int C, int ST, int S>
 size_t cr_smem_bytes(int NT) {
   using CT = typename StorageType<ST>::compute;
-  return sizeof(CT) * ((size_t)NT * S + (size_t)4 * C * NT);
+  return sizeof(CT) * ((size_t)NT * S + (size_t)4 * C * kCRThreads);
 }
 
 #define LBKS_COLLAPSE_CASES(OP)                                                         \
