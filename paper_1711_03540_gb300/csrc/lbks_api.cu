@@ -497,12 +497,16 @@ cudaError_t prepared(int kind, int Q, int prec, int S, int NT, int* out) {
 // Resident kernel plan.  Whole lattices (rings) run k_ring steps per launch; lattices
 // cut into segments run k_seg-step launches (their halo grows with the steps per
 // launch).  Rings of up to NT S sites run in single-block work groups; with cl = 2,
-// rings of up to 2 NT S sites run whole in cluster pairs (with smaller rings filling
-// the pairs' spare threads) instead of being cut into segments.  The kinds present run
-// as concurrent lanes on disjoint sets of blocks, on their own streams, sized so that
-// all finish a chunk of steps at about the same time.  S_force / NT_force / cl_force
-// > 0 pin the tiling (autotuner trials); lane_weight is the cost of a pair or segment
-// bundle relative to a single-block ring bundle, used to split the blocks.
+// rings of up to 2 NT S sites run in cluster pairs, as two haloed halves (halo
+// exchanged every kx steps) when a half with its halos fits a block, else as one ring
+// across both blocks, with smaller rings filling the pairs' spare threads, instead of
+// being cut into segments.  The kinds present run as concurrent lanes on disjoint sets
+// of blocks, on their own streams, sized so that all finish a chunk of steps at about
+// the same time; or (merge = 1, or by default when the pairs hold more threads than the
+// single blocks) the single-block bundles go two to a pair on the pair lane's queue.
+// S_force / NT_force / cl_force > 0 pin the tiling and kx_force >= 0 the exchange
+// interval (0: no halves) for autotuner trials; lane_weight is the cost of a pair or
+// segment bundle relative to a single-block ring bundle, used to split the blocks.
 int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, double lane_weight = 1.25,
                    int cl_force = 0, int merge = -1, int kx_force = -1) {
   const bool col = h->nplanes == 1;  // the tau = 1 collapse's resident kernel
