@@ -992,21 +992,34 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   }
   h->plane = std::max<int64_t>(off, kAlign);
 
-  // Tiles.
-  std::vector<Tile> pt, st;
+  // Tiles.  The streaming tiles (also those of the guard, the statistics of rho0 and the
+  // gathers) always; the plain family's only when a kernel that uses them runs (the
+  // plain and reservoir steps, the collapse's initialisation).
+  std::vector<Tile> st;
   std::vector<int32_t> st_begin(nruns + 1);
   const int TS = stream_tile_sites();
   for (int32_t r = 0; r < nruns; ++r) {
-    // reservoir lattices: the plain-family tiles also cover the ghost nodes
-    const int64_t g0 = reservoir ? -cmax : 0, g1 = reservoir ? N[r] + cmax : N[r];
-    for (int64_t x = g0; x < g1; x += kPlainTile)
-      pt.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(kPlainTile, g1 - x), 0});
     st_begin[r] = (int32_t)st.size();
     for (int64_t x = 0; x < N[r]; x += TS) st.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(TS, N[r] - x), 0});
   }
   st_begin[nruns] = (int32_t)st.size();
-  h->n_plain_tiles = (int)pt.size();
   h->n_stream_tiles = (int)st.size();
+  auto plain_tiles = [&]() -> int {
+    if (h->d_plain_tiles) return LB_KS_OK;
+    std::vector<Tile> pt;
+    for (int32_t r = 0; r < nruns; ++r) {
+      // reservoir lattices: the plain-family tiles also cover the ghost nodes
+      const int64_t g0 = reservoir ? -cmax : 0, g1 = reservoir ? N[r] + cmax : N[r];
+      for (int64_t x = g0; x < g1; x += kPlainTile)
+        pt.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(kPlainTile, g1 - x), 0});
+    }
+    int rc2;
+    if ((rc2 = dalloc(h, &h->d_plain_tiles, pt.size()))) return rc2;
+    cudaError_t e2 = cudaMemcpy(h->d_plain_tiles, pt.data(), sizeof(Tile) * pt.size(), cudaMemcpyHostToDevice);
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "upload plain tiles");
+    h->n_plain_tiles = (int)pt.size();
+    return LB_KS_OK;
+  };
 
   int rc;
   const size_t fbytes = storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane;
@@ -1017,7 +1030,6 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     if ((ce = cudaMemset(p, 0, fbytes)) != cudaSuccess) return bail(cuda_fail(h, ce, "clear populations"));
   }
   if ((rc = dalloc(h, &h->d_runs, nruns))) return bail(rc);
-  if ((rc = dalloc(h, &h->d_plain_tiles, pt.size()))) return bail(rc);
   if ((rc = dalloc(h, &h->d_stream_tiles, st.size()))) return bail(rc);
   if ((rc = dalloc(h, &h->d_stream_tile_begin, st_begin.size()))) return bail(rc);
   if ((rc = dalloc(h, &h->d_rho_off, h->rho_off.size()))) return bail(rc);
@@ -1031,7 +1043,6 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   if ((rc = dalloc(h, &h->d_bad_run, 1))) return bail(rc);
   auto up = [&](void* dst, const void* src, size_t bytes) { return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice); };
   if ((ce = up(h->d_runs, h->runs_h.data(), sizeof(RunDesc) * nruns)) != cudaSuccess ||
-      (ce = up(h->d_plain_tiles, pt.data(), sizeof(Tile) * pt.size())) != cudaSuccess ||
       (ce = up(h->d_stream_tiles, st.data(), sizeof(Tile) * st.size())) != cudaSuccess ||
       (ce = up(h->d_stream_tile_begin, st_begin.data(), sizeof(int32_t) * st_begin.size())) != cudaSuccess ||
       (ce = up(h->d_rho_off, h->rho_off.data(), sizeof(int64_t) * h->rho_off.size())) != cudaSuccess ||
@@ -1102,6 +1113,8 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   }
   if (h->nlanes > 1 && !h->ev_fork) return bail(fail(h, LB_KS_ECUDA, "internal: lanes without their streams"));
 
+  if ((kern == LB_KS_KERNEL_COLLAPSE || kern == LB_KS_KERNEL_PLAIN || reservoir) && (rc = plain_tiles()) != LB_KS_OK)
+    return bail(rc);
   if (kern == LB_KS_KERNEL_COLLAPSE) {
     // rho - rhobar in both arenas (reservoir ends and ghosts keep their values in both)
     for (int b = 0; b < 2; ++b)
