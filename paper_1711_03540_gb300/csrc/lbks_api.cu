@@ -1213,10 +1213,26 @@ int lb_ks_rho(lb_ks_t* h, double* out) {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   if (h->sticky) return h->sticky;
   if (!out) return fail(h, LB_KS_EINVAL, "out must not be NULL");
+  // The gather writes straight into out when the device can address it (memory of this
+  // device, or pinned host memory mapped into the device's address space, which on a
+  // coherent host link costs no extra pass); other host memory gets a staged copy.
+  double* dst = h->d_stage;
+  {
+    int dev = 0;
+    cudaPointerAttributes pa{};
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaPointerGetAttributes(&pa, out) == cudaSuccess) {
+      if ((pa.type == cudaMemoryTypeDevice && pa.device == dev) || (pa.type == cudaMemoryTypeHost && pa.devicePointer))
+        dst = static_cast<double*>(pa.devicePointer);
+    } else {
+      cudaGetLastError();
+    }
+  }
   LBKS_CUDA(h, launch_gather_rho(h->nplanes, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles, h->n_stream_tiles,
-                                 h->d_stage, h->d_rho_off, h->stream), "gather rho");
+                                 dst, h->d_rho_off, h->stream), "gather rho");
   h->launches += 1;
-  LBKS_CUDA(h, cudaMemcpyAsync(out, h->d_stage, sizeof(double) * (size_t)h->total_sites, cudaMemcpyDefault, h->stream), "copy rho");
+  if (dst == h->d_stage)
+    LBKS_CUDA(h, cudaMemcpyAsync(out, h->d_stage, sizeof(double) * (size_t)h->total_sites, cudaMemcpyDefault, h->stream),
+              "copy rho");
   LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   return check_flags(h);
 }
