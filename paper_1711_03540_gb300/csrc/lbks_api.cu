@@ -14,6 +14,7 @@
 
 #include "../../include/lb_ks.h"
 #include "lbks_internal.h"
+#include "lbks_plan.h"
 
 namespace lbks {
 int stream_tile_sites();
@@ -21,6 +22,7 @@ cudaError_t stream_prepare(int Q, int storage);
 }
 
 using namespace lbks;
+using namespace lbks::plan;
 
 namespace {
 
@@ -220,233 +222,6 @@ bool valid_opts(const lb_ks_opts& o, std::string* why) {
 
 bool has_pair_lattices(const lb_ks* h, int S, int NT);
 
-// One half of a ring of N sites for a cluster pair: own sites [x_own, x_own + len) of
-// the ring with `halo` sites on each side, lengthened on the right until it splits
-// into runs of S and S-1 sites; false if that takes more than NT threads.
-bool plan_half(int32_t r, int64_t N, int64_t x_own, int64_t len, int halo, int S, int NT, Piece* p) {
-  int64_t n = len + 2 * halo;
-  int64_t V = (n + S - 1) / S;
-  while (n <= V * (S - 1)) { ++n; V = (n + S - 1) / S; }
-  if (V > NT) return false;
-  *p = Piece{};
-  p->run = r; p->t0 = 0; p->nthr = (int)V; p->n = (int)n;
-  p->x0 = ((x_own - halo) % N + N) % N;
-  p->st_lo = halo; p->st_hi = (int)(halo + len);
-  p->halo = halo;
-  return true;
-}
-
-// Pieces of every run for (S, NT): rings (whole lattices held by at most ring_cap
-// threads: NT, or 2 NT for two-block clusters) and segments (for longer lattices,
-// held by one block each, with c_max * kseg halo sites per side); false if some
-// run cannot be held.  With two-block clusters and kx > 0, a lattice longer than one
-// block holds is split into two halves (consecutive in `rings`, halo c_max kx) when
-// each half with its halos fits one block, instead of one ring across both blocks.
-bool plan_pieces(const lb_ks* h, int S, int NT, int ring_cap, int kseg, int kx, std::vector<Piece>* rings,
-                 std::vector<Piece>* segs) {
-  rings->clear();
-  segs->clear();
-  const int C = h->cmax;
-  for (int32_t r = 0; r < h->nruns; ++r) {
-    const int64_t N = h->N[r];
-    // Ring: hold m copies of the lattice around one ring of m N sites (m > 1 only
-    // for lattices shorter than S (S-1), which cannot be cut into runs of S and
-    // S-1 sites).  Translation invariance keeps the copies bitwise identical;
-    // the first one is stored.
-    bool ring = false;
-    for (int64_t m = 1;; ++m) {
-      const int64_t n = m * N;
-      const int64_t V = (n + S - 1) / S;
-      if (V > ring_cap) break;
-      if (n > V * (S - 1)) {
-        if (V > NT && kx > 0) {
-          const int halo = C * kx;
-          const int64_t NA = (N + 1) / 2, NB = N - NA;
-          Piece a{}, b{};
-          if (NB >= 2 * halo && plan_half(r, N, 0, NA, halo, S, NT, &a) && plan_half(r, N, NA, NB, halo, S, NT, &b)) {
-            rings->push_back(a);
-            rings->push_back(b);
-            ring = true;
-            break;
-          }
-        }
-        Piece p{};
-        p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n; p.x0 = 0; p.st_lo = 0; p.st_hi = (int)N;
-        rings->push_back(p);
-        ring = true;
-        break;
-      }
-    }
-    if (ring) continue;
-    const int64_t h2 = 2LL * C * kseg;
-    const int64_t room = (int64_t)NT * S - h2 - 2 * S;
-    if (room <= 0) return false;
-    const int64_t nseg = (N + room - 1) / room;
-    const int64_t Ls = (N + nseg - 1) / nseg;
-    for (int64_t s0 = 0; s0 < N; s0 += Ls) {
-      const int64_t len = std::min<int64_t>(Ls, N - s0);
-      int64_t n = len + h2;
-      int64_t V = (n + S - 1) / S;
-      while (n <= V * (S - 1)) { ++n; V = (n + S - 1) / S; }
-      if (V > NT) return false;
-      Piece p{};
-      p.run = r; p.t0 = 0; p.nthr = (int)V; p.n = (int)n;
-      p.x0 = ((s0 - (int64_t)C * kseg) % N + N) % N;
-      p.st_lo = C * kseg; p.st_hi = (int)(C * kseg + len);
-      segs->push_back(p);
-    }
-  }
-  return true;
-}
-
-// Work groups of one lane during packing: first fit of pieces (threads nthr) into
-// groups of `cap` threads.
-struct Bins {
-  int cap = 0;
-  bool pair = false;  // pair work groups: block 0 is threads [0, cap/2), block 1 the rest
-  std::vector<std::vector<int>> members;
-  std::vector<int> used;   // threads [0, used) taken (pair work groups: the end of block 1's)
-  std::vector<int> used0;  // pair work groups: threads [0, used0) of block 0 taken
-  std::vector<int> key;    // queue order (largest first); empty: by occupied threads
-  // Segment tree of the largest free run (block 0's or block 1's) over the groups, so
-  // that first fit finds the first group with room in O(log groups).
-  std::vector<int> tree;
-  size_t tn = 0;
-
-  int room(size_t b) const {
-    int f = cap - used[b];
-    if (pair) f = std::max(f, cap / 2 - used0[b]);
-    return f;
-  }
-  void fix(size_t b) {
-    if (b >= tn) {
-      tn = std::max<size_t>(64, 2 * tn);
-      while (tn <= b) tn *= 2;
-      tree.assign(2 * tn, -1);
-      for (size_t q = 0; q < used.size(); ++q) tree[tn + q] = room(q);
-      for (size_t p = tn - 1; p >= 1; --p) tree[p] = std::max(tree[2 * p], tree[2 * p + 1]);
-      return;
-    }
-    size_t p = tn + b;
-    tree[p] = room(b);
-    for (p >>= 1; p >= 1; p >>= 1) tree[p] = std::max(tree[2 * p], tree[2 * p + 1]);
-  }
-  // A new group holding pieces `mem`, with u0 threads of block 0 (pair groups) and
-  // threads [0, u) (pair groups: block 1's up to u) taken.
-  void add(std::vector<int> mem, int u0, int u) {
-    members.push_back(std::move(mem));
-    used.push_back(u);
-    if (pair) used0.push_back(u0);
-    fix(used.size() - 1);
-  }
-  // First fit: the first group with room for the piece.  A piece never spans the
-  // block edge of a pair work group here: it goes into block 0's free threads or
-  // after block 1's taken ones.
-  bool first_fit(std::vector<Piece>& pieces, int i) {
-    const int need = pieces[i].nthr;
-    if (tn == 0 || tree[1] < need) return false;
-    size_t p = 1;
-    while (p < tn) p = tree[2 * p] >= need ? 2 * p : 2 * p + 1;
-    const size_t b = p - tn;
-    if (pair && used0[b] + need <= cap / 2) {
-      pieces[i].t0 = used0[b];
-      used0[b] += need;
-    } else {
-      pieces[i].t0 = used[b];
-      used[b] += need;
-    }
-    members[b].push_back(i);
-    fix(b);
-    return true;
-  }
-  void open(std::vector<Piece>& pieces, int i) {
-    pieces[i].t0 = 0;
-    add({i}, 0, pieces[i].nthr);
-  }
-  // bundles in decreasing order of occupied threads (longest first)
-  void emit(const std::vector<Piece>& pieces, std::vector<Piece>* ordered, std::vector<int2>* bundles) const {
-    std::vector<int> order(members.size());
-    for (size_t b = 0; b < members.size(); ++b) order[b] = (int)b;
-    const std::vector<int>& kk = key.empty() ? used : key;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kk[a] > kk[b]; });
-    ordered->clear();
-    bundles->clear();
-    for (int b : order) {
-      bundles->push_back(make_int2((int)ordered->size(), (int)members[b].size()));
-      for (int i : members[b]) ordered->push_back(pieces[i]);
-    }
-  }
-};
-
-std::vector<int> by_threads_desc(const std::vector<Piece>& pieces) {
-  std::vector<int> idx(pieces.size());
-  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return pieces[a].nthr > pieces[b].nthr; });
-  return idx;
-}
-
-// First-fit decreasing packing of whole lattices: a lattice held as two halves opens a
-// cluster pair (one half at the start of each block), one longer than one block (more
-// than NT threads) opens a pair as a ring across both blocks; the others fill the
-// pairs' spare threads first, then blocks of NT threads.
-void pack_rings(std::vector<Piece>& pieces, int NT, Bins* blocks, Bins* pairs) {
-  blocks->cap = NT;
-  pairs->cap = 2 * NT;
-  pairs->pair = true;
-  for (size_t i = 0; i + 1 < pieces.size(); ++i) {
-    if (pieces[i].halo == 0) continue;
-    pieces[i].t0 = 0;
-    pieces[i + 1].t0 = NT;
-    pairs->add({(int)i, (int)i + 1}, pieces[i].nthr, NT + pieces[i + 1].nthr);
-    ++i;
-  }
-  for (int i : by_threads_desc(pieces)) {
-    if (pieces[i].halo > 0) continue;
-    if (pieces[i].nthr > NT) {
-      pieces[i].t0 = 0;
-      pairs->add({i}, NT, pieces[i].nthr);
-    } else if (!pairs->first_fit(pieces, i) && !blocks->first_fit(pieces, i)) {
-      blocks->open(pieces, i);
-    }
-  }
-  pairs->key.resize(pairs->used.size());
-  for (size_t b = 0; b < pairs->used.size(); ++b) pairs->key[b] = pairs->used0[b] + pairs->used[b] - NT;
-}
-
-// One queue for every whole lattice: the single-block bundles go two to a cluster
-// pair (the second one's pieces shifted by NT threads, so no piece spans the block
-// edge and its blocks never wait on each other), queued after the pair bundles whose
-// piece spans the edge; within each kind, largest first.
-// (Groups appended here take no further pieces.)
-void merge_blocks_into_pairs(std::vector<Piece>& pieces, int NT, const Bins& blocks, Bins* pairs) {
-  pairs->cap = 2 * NT;
-  for (size_t b = 0; b < pairs->key.size(); ++b) pairs->key[b] += 4 * NT;
-  std::vector<int> order(blocks.members.size());
-  for (size_t b = 0; b < order.size(); ++b) order[b] = (int)b;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blocks.used[a] > blocks.used[b]; });
-  for (size_t q = 0; q < order.size(); q += 2) {
-    std::vector<int> mem = blocks.members[order[q]];
-    int used = blocks.used[order[q]];
-    if (q + 1 < order.size()) {
-      for (int i : blocks.members[order[q + 1]]) {
-        pieces[i].t0 += NT;
-        mem.push_back(i);
-      }
-      used = NT + blocks.used[order[q + 1]];
-    }
-    pairs->members.push_back(mem);
-    pairs->used.push_back(used);
-    pairs->used0.push_back(blocks.used[order[q]]);
-    pairs->key.push_back(blocks.used[order[q]]);  // the fuller of the two blocks
-  }
-}
-
-void pack_blocks(std::vector<Piece>& pieces, int NT, Bins* blocks) {
-  blocks->cap = NT;
-  for (int i : by_threads_desc(pieces))
-    if (!blocks->first_fit(pieces, i)) blocks->open(pieces, i);
-}
-
 int default_threads(int prec, int S) {
   if (prec == kF64) return 256;
   return S <= 8 ? 512 : (S <= 12 ? 384 : 256);
@@ -535,7 +310,7 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
     if (col) cl = 1;  // no cluster variant of the collapse
     std::vector<Piece> rings, segs;
     const int kx = cl == 2 ? (kx_force >= 0 ? kx_force : kPairSteps) : 0;
-    if (!plan_pieces(h, S, NT, cl * NT, kseg, kx, &rings, &segs)) continue;
+    if (!plan_pieces(h->N, h->cmax, S, NT, cl * NT, kseg, kx, &rings, &segs)) continue;
     Bins blocks, pairs, segbins;
     pack_rings(rings, NT, &blocks, &pairs);
     // default: one queue of pair work groups when the pairs hold most of the threads
