@@ -250,6 +250,14 @@ LB_KS_API int lb_ks_state_bytes(const lb_ks_t *h, size_t *bytes);
  * at the sum of the rounded sizes of the runs before it.  Populations are
  * stored as f_0 - rhobar, f_1, ..., f_{Q-1} (divided by the run's scale for
  * F16S), rhobar and scale being the run's initial mean and storage scale.
+ * lb_ks_load returns LB_KS_EINVAL, leaving the handle as it was, when the
+ * buffer is shorter than lb_ks_state_bytes, its header (scheme, precision,
+ * runs, plane) or lattice sizes differ from the handle's, a run record places
+ * its run elsewhere in the arenas than the handle does (or differs in its
+ * ends), a run's constants are not finite, or a step counter is negative.
+ * The steps since the last guard are taken modulo this handle's
+ * recentre_every, which may differ from the saving handle's.  A successful
+ * load clears a sticky device error.
  */
 LB_KS_API int lb_ks_save(lb_ks_t *h, void *buf, size_t bytes);
 LB_KS_API int lb_ks_load(lb_ks_t *h, const void *buf, size_t bytes);

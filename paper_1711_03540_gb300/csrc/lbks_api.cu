@@ -1078,9 +1078,20 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
   if (std::memcmp(p, h->N.data(), sizeof(int64_t) * h->nruns) != 0)
     return fail(h, LB_KS_EINVAL, "checkpoint lattice sizes differ from this handle's");
   p += sizeof(int64_t) * h->nruns;
+  if (hdr2[1] < 0 || hdr2[2] < 0) return fail(h, LB_KS_EINVAL, "checkpoint step counters are negative");
   std::vector<RunDesc> runs(h->nruns);
   std::memcpy(runs.data(), p, sizeof(RunDesc) * h->nruns);
   p += sizeof(RunDesc) * h->nruns;
+  // the constants (coefficients, rhobar, storage scale) come from the checkpoint; where
+  // each run lies in the arenas, and its ends, must be this handle's (the kernels index by them)
+  for (int32_t r = 0; r < h->nruns; ++r) {
+    const RunDesc &c = runs[r], &own = h->runs_h[r];
+    if (c.off != own.off || c.N != own.N || c.reservoir != own.reservoir)
+      return fail(h, LB_KS_EINVAL, "checkpoint run " + std::to_string(r) + ": layout differs from this handle's");
+    bool finite = std::isfinite(c.r) && std::isfinite(c.rhobar) && std::isfinite(c.scale) && c.scale > 0.0;
+    for (int i = 0; i < h->Q; ++i) finite = finite && std::isfinite(c.a[i]) && std::isfinite(c.b[i]);
+    if (!finite) return fail(h, LB_KS_EINVAL, "checkpoint run " + std::to_string(r) + ": constants are not finite");
+  }
   std::vector<double> m0(h->nruns);
   std::memcpy(m0.data(), p, sizeof(double) * h->nruns);
   p += sizeof(double) * h->nruns;
@@ -1092,7 +1103,10 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
   LBKS_CUDA(h, cudaMemcpy(h->fbuf[h->cur], p, storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane,
                           cudaMemcpyHostToDevice), "load populations");
   h->steps_done = hdr2[1];
-  h->phase = hdr2[2];
+  // steps since the last guard, on this handle's guard interval (which may differ from
+  // the saving handle's): a phase at or past it would never meet it again
+  const int64_t R = h->opts.recentre_every;
+  h->phase = R > 0 ? hdr2[2] % R : 0;
   h->sticky = LB_KS_OK;
   LBKS_CUDA(h, cudaMemset(h->d_flags, 0, sizeof(int)), "clear flags");
   return LB_KS_OK;

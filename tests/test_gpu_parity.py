@@ -247,6 +247,57 @@ def test_checkpoint_resume_bitwise(lb, prec):
     np.testing.assert_array_equal(ra, rb)
 
 
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_checkpoint_load_validates_and_rebases_guard_phase(lb, use_graph):
+    """A checkpoint taken 400 steps after a guard of a handle that recentres every 500
+    loads into one that recentres every 100 (phase 400 mod 100 = 0: guards 100 and 200
+    steps on, after which the mass is the initial one to the storage granularity) and
+    steps on; a record that moves a run in the arenas, a non-finite constant or a
+    negative step counter gives EINVAL and leaves the handle as it was."""
+    Ns = np.array([700, 2500], dtype=np.int64)
+    rng = np.random.default_rng(5)
+    r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
+    mk = lambda every: lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(2, 1e-4), np.array([1.7, 2.9]), r0,
+                                           lb.lb_ks_default_opts(precision=1, recentre_every=every,
+                                                                 use_graph=use_graph))
+    a = mk(500)
+    b = None
+    try:
+        lb.lb_ks_step(a, 400)
+        buf = np.zeros(lb.lb_ks_state_bytes(a), dtype=np.uint8)
+        lb.lb_ks_save(a, buf)
+        b = mk(100)
+        plane = int(sum((n + 31) // 32 * 32 for n in Ns))
+        rec = (buf.size - 64 - 16 * Ns.size - 4 * 7 * plane) // Ns.size  # bytes of one run record
+        base = 64 + 8 * Ns.size  # the run records: off (int64) first, N, then a[0] (double)
+        for corrupt, why in (
+                (lambda v: v[base + rec:base + rec + 8].view(np.int64).__iadd__(32), "layout differs"),
+                (lambda v: v[base + 16:base + 24].view(np.float64).__setitem__(0, np.nan), "not finite"),
+                (lambda v: v[40:48].view(np.int64).__setitem__(0, -1), "negative")):
+            bad = buf.copy()
+            corrupt(bad)
+            with pytest.raises(lb.LbKsError) as e:
+                lb.lb_ks_load(b, bad)
+            assert e.value.code == -1 and why in lb.lb_ks_last_error(b)
+            assert lb.lb_ks_steps_done(b) == 0
+        lb.lb_ks_load(b, buf)
+        assert lb.lb_ks_steps_done(b) == 400
+        lb.lb_ks_step(b, 200)
+        mb = np.empty(2)
+        lb.lb_ks_mass_energy(b, mb, None)  # right after the guard 200 steps on
+        lb.lb_ks_step(b, 50)
+        assert lb.lb_ks_steps_done(b) == 650
+        rb = np.empty(r0.size)
+        lb.lb_ks_rho(b, rb)
+    finally:
+        lb.lb_ks_free(a)
+        if b is not None:
+            lb.lb_ks_free(b)
+    assert np.all(np.isfinite(rb))
+    m0 = np.array([r0[:700].sum(), r0[700:].sum()])
+    assert np.all(np.abs(mb - m0) <= 2 * np.ceil(Ns / 1024) * 2.0 ** -24)
+
+
 def _mass_after(lb, Ns, r0, prec, every, n):
     # streaming kernel: the populations are rounded to the storage precision every step
     h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(Ns.size, 1e-4), np.linspace(1.5, 3.0, Ns.size), r0,
