@@ -200,20 +200,22 @@ def run_reference(args):
     from paper_1711_03540_gb300 import workloads
 
     wl = workloads.ensemble(nruns=args.nruns)
-    vals = []
+    vals, used = [], 1
     for _ in range(args.warmup):
         cpu_baseline(wl, sample_runs=8, sample_steps=50)
     t_all = 0.0
     for _ in range(args.steps):
         r = cpu_baseline(wl, sample_runs=16, sample_steps=100)
         vals.append(r["value"])
+        used = max(used, r["cores"])
         t_all += r["seconds"]
     v = float(statistics.median(vals))
     line = {"impl": "reference", "metric": "lattice-site updates/s", "value": v, "unit": "site-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "sample": "16 runs x 100 LB steps per step"},
-            "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+            "config": {"workload": wl.name, "scheme": f"D1Q{wl.scheme}", "nruns": wl.nruns, "sites": int(wl.sites),
+                       "sample": "16 runs x 100 LB steps per step"},
+            "cpu_baseline": {"value": v, "unit": "site-updates/s", "cores": used, "kind": "oracle",
                              "sample": "16 of 4096 runs (evenly spaced), 100 LB steps, FP64"},
             "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
