@@ -7,7 +7,11 @@
 // threads from the neighbouring sites, periodic wrap).  After one barrier
 // every thread reads the shifted values f*_i(x - c_i) for lane-contiguous
 // sites and stores them coalesced.  HBM traffic per site-update: one read and
-// one write of the Q populations (plus 2 c_max halo sites per tile).
+// one write of the Q populations (plus 2 c_max halo sites per tile).  Scaled
+// FP16 storage keeps the tile in shared memory as halves (rounded once, in the
+// collision phase) and stores two adjacent sites per thread with one 4-byte store.
+#include <type_traits>
+
 #include "lbks_device.cuh"
 
 namespace lbks {
@@ -42,6 +46,12 @@ template <> struct Vec4<__half> {
   }
 };
 
+// Element type of the shared-memory tile: the storage type for scaled FP16 (the
+// value is rounded to it once, where it is computed), else the compute type.
+template <int ST>
+using TileType = typename std::conditional<ST == kF16S, typename StorageType<ST>::type,
+                                           typename StorageType<ST>::compute>::type;
+
 // Aligned 16-byte shared-memory stores of kVec post-collision values of plane i
 // (conflict-free; the tile row stride Q*W*sizeof(CT) is a multiple of 16 bytes).
 template <int Q>
@@ -54,16 +64,35 @@ __device__ __forceinline__ void store4(double* p, const double (&g)[kVec][Q], in
   reinterpret_cast<double2*>(p)[1] = make_double2(g[2][i], g[3][i]);
 }
 
+// Four scaled FP16 values of plane i, rounded to storage, as one aligned 8-byte store.
+template <int Q>
+__device__ __forceinline__ void store4_half(__half* p, const float (&g)[kVec][Q], int i, float inv_scale) {
+  __half o[kVec];
+#pragma unroll
+  for (int u = 0; u < kVec; ++u) from_compute(g[u][i], inv_scale, &o[u]);
+  const __half2 a = __halves2half2(o[0], o[1]), b = __halves2half2(o[2], o[3]);
+  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
 template <int Q, int ST>
 __global__ void __launch_bounds__(kStreamThreads) stream_step_kernel(Arena src, Arena dst,
                                                                      const RunDesc* __restrict__ runs,
                                                                      const Tile* __restrict__ tiles) {
   using T = typename StorageType<ST>::type;
   using CT = typename StorageType<ST>::compute;
+  using ET = TileType<ST>;
+  constexpr bool kHalf = ST == kF16S;
   constexpr int C = cmax_of(Q);
   constexpr int W = kTile + 2 * kHalo;
+  static_assert(W % 8 == 0, "tile rows of halves must start 16-byte aligned");
+  static_assert(C < kHalo, "the paired FP16 reads reach column kHalo - c_max - 1");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CT* sm = reinterpret_cast<CT*>(smem_raw);  // [Q][W], tile site k at column kHalo + k
+  ET* sm = reinterpret_cast<ET*>(smem_raw);  // [Q][W], tile site k at column kHalo + k
+  // one tile value, rounded to the tile's element type
+  auto put = [&](ET* p, CT v, CT inv_scale) {
+    if constexpr (kHalf) from_compute(v, inv_scale, p);
+    else *p = v;
+  };
 
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
@@ -97,13 +126,16 @@ __global__ void __launch_bounds__(kStreamThreads) stream_step_kernel(Arena src, 
       for (int u = 0; u < kVec; ++u) collide<Q, CT>(g[u], k);
       if (k0 + kVec <= len) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) store4(sm + i * W + kHalo + k0, g, i);
+        for (int i = 0; i < Q; ++i) {
+          if constexpr (kHalf) store4_half(sm + i * W + kHalo + k0, g, i, k.inv_scale);
+          else store4(sm + i * W + kHalo + k0, g, i);
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i)
 #pragma unroll
           for (int u = 0; u < kVec; ++u)
-            if (k0 + u < len) sm[i * W + kHalo + k0 + u] = g[u][i];
+            if (k0 + u < len) put(&sm[i * W + kHalo + k0 + u], g[u][i], k.inv_scale);
       }
     }
     // Halo: C sites left of the tile and C sites right of it (periodic in the run).
@@ -116,21 +148,43 @@ __global__ void __launch_bounds__(kStreamThreads) stream_step_kernel(Arena src, 
       for (int i = 0; i < Q; ++i) g[i] = to_compute(fs[(int64_t)i * src.plane + xs], k.scale);
       collide<Q, CT>(g, k);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) sm[i * W + col] = g[i];
+      for (int i = 0; i < Q; ++i) put(&sm[i * W + col], g[i], k.inv_scale);
     }
   }
   __syncthreads();
   // Phase 2: pull f*_i(x - c_i), lane-contiguous sites, coalesced stores.
+  if constexpr (kHalf) {
+    // Sites kk and kk + 1 (kk even) of plane i sit at tile columns e and e + 1,
+    // e = kHalo + kk - c_i; W and kHalo are even, so for even c_i they are one aligned
+    // 32-bit word, for odd c_i the high half of word (e - 1) / 2 and the low half of
+    // the next.  Columns read stay in [kHalo - 4, kHalo + kTile + 3] = [0, W) of the
+    // row (c_max <= 3 <= kHalo - 1); a value read past a ragged tile's end or its halo
+    // is not stored.  Rows, run offsets, the plane stride and tile starts are even, so
+    // the 4-byte global stores are aligned.
+    const uint32_t* sw = reinterpret_cast<const uint32_t*>(smem_raw);
 #pragma unroll
-  for (int u = 0; u < kVec; ++u) {
-    const int kk = threadIdx.x + u * kStreamThreads;
-    if (kk < len) {
+    for (int u = 0; u < kVec / 2; ++u) {
+      const int kk = 2 * (threadIdx.x + u * kStreamThreads);
+      if (kk < len) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const CT v = sm[i * W + kHalo + kk - speed(i)];
-        T out;
-        from_compute(v, k.inv_scale, &out);
-        __stcs(fd + (int64_t)i * dst.plane + x0 + kk, out);
+        for (int i = 0; i < Q; ++i) {
+          const int e = i * W + kHalo + kk - speed(i);
+          uint32_t w;
+          if ((speed(i) & 1) == 0) w = sw[e >> 1];
+          else w = __byte_perm(sw[(e - 1) >> 1], sw[(e + 1) >> 1], 0x5432);
+          T* p = fd + (int64_t)i * dst.plane + x0 + kk;
+          if (kk + 1 < len) __stcs(reinterpret_cast<unsigned int*>(p), w);
+          else __stcs(p, __ushort_as_half((unsigned short)(w & 0xffffu)));
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < kVec; ++u) {
+      const int kk = threadIdx.x + u * kStreamThreads;
+      if (kk < len) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) __stcs(fd + (int64_t)i * dst.plane + x0 + kk, sm[i * W + kHalo + kk - speed(i)]);
       }
     }
   }
@@ -138,8 +192,7 @@ __global__ void __launch_bounds__(kStreamThreads) stream_step_kernel(Arena src, 
 
 template <int Q, int ST>
 size_t stream_smem() {
-  using CT = typename StorageType<ST>::compute;
-  return sizeof(CT) * Q * (kTile + 2 * kHalo);
+  return sizeof(TileType<ST>) * Q * (kTile + 2 * kHalo);
 }
 
 template <int Q, int ST>

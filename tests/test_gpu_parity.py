@@ -135,11 +135,14 @@ def test_autotuned_handle_starts_from_rho0(lb):
     np.testing.assert_array_equal(ref, out)
 
 
-def test_f16s_resident_one_step_per_launch_equals_stream(lb):
-    Ns = np.array([640, 2000], dtype=np.int64)
+@pytest.mark.parametrize("Q", [5, 7])
+def test_f16s_resident_one_step_per_launch_equals_stream(lb, Q):
+    """Scaled FP16: the streaming step (FP16 tile, two sites per store) equals the
+    resident kernel at one step per launch bitwise, on even and odd tile tails."""
+    Ns = np.array([640, 2000, 1027, 333, Q, 4097, 2048], dtype=np.int64)
     rng = np.random.default_rng(4)
     r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
-    args = (7, Ns, Ns * 0.1, np.full(2, 1e-4), np.array([1.5, 2.5]), r0, 50)
+    args = (Q, Ns, Ns * 0.1, np.full(Ns.size, 1e-4), np.linspace(1.5, 2.5, Ns.size), r0, 50)
     a = run_gpu(lb, *args, precision=2, kernel=2)[0]
     b = run_gpu(lb, *args, precision=2, kernel=3, steps_per_launch=1)[0]
     np.testing.assert_array_equal(a, b)
