@@ -15,8 +15,10 @@
  *
  * Conventions shared by every entry point:
  *  - Every function returns a status code (LB_KS_OK or a negative LB_KS_E*);
- *    no C++ exception crosses this boundary.  lb_ks_last_error() gives a
- *    one-line reason for the last failure on a handle.
+ *    no C++ exception crosses this boundary: a host allocation that fails
+ *    inside a call returns LB_KS_ENOMEM (inside lb_ks_step it is also sticky,
+ *    since the handle's step count may then be ahead of the work issued).
+ *    lb_ks_last_error() gives a one-line reason for the last failure on a handle.
  *  - A handle owns its device memory (allocated in lb_ks_init /
  *    lb_ks_batch_init, released by lb_ks_free).  It never keeps or frees a
  *    pointer the caller passes in.  Input and output pointers may be host or
@@ -170,8 +172,8 @@ LB_KS_API int lb_ks_max_growth(int scheme, double dx, double dt, double tau, int
  * 0.908 and the paper uses tau >= 1, Sec. 3), and initial density
  * rho0[N] (FP64, host or device, read once).  Populations start at
  * equilibrium, f_i = f^eq_i(rho0).  opts may be NULL (defaults).
- * Errors: LB_KS_EINVAL (unknown scheme, N < 2 c_max + 1, L <= 0, dt <= 0,
- * tau < 1, non-finite rho0, bad opts), LB_KS_ENOMEM, LB_KS_ECUDA.  On error
+ * Errors: LB_KS_EINVAL (unknown scheme, N < 2 c_max + 1 or N > 2^30, L <= 0,
+ * dt <= 0, tau < 1, non-finite rho0, bad opts), LB_KS_ENOMEM, LB_KS_ECUDA.  On error
  * *h is set to NULL.  Not an error: when the linear check of lb_ks_max_growth
  * (nk = 128, about rho = 0) finds the run unstable, the handle is created and
  * lb_ks_last_error(h) starts with "warning:" (batch handles: checked when the
@@ -185,7 +187,9 @@ LB_KS_API int lb_ks_init(lb_ks_t **h, int scheme, int64_t N, double L, double dt
  * (one ensemble).  Run r has N[r] sites on [0, L[r]), time step dt[r] and
  * relaxation time tau[r]; rho0 holds the initial densities of all runs
  * concatenated in run order (sum N[r] values, FP64, host or device).
- * The same argument rules and errors as lb_ks_init apply to every run.
+ * The same argument rules and errors as lb_ks_init apply to every run; a
+ * batch of more than 2^34 sites in all (more than the device's memory holds in
+ * any storage) is LB_KS_EINVAL.
  */
 LB_KS_API int lb_ks_batch_init(lb_ks_t **h, int scheme, int32_t nruns, const int64_t *N, const double *L,
                      const double *dt, const double *tau, const double *rho0, const lb_ks_opts *opts);

@@ -32,6 +32,10 @@ constexpr int kPlainTile = 256;
 constexpr int kAlign = 32;  // elements: run offsets and the plane stride are multiples of this
 constexpr uint32_t kMagic = 0x534b424cu;  // "LBKS"
 constexpr uint32_t kVersion = 1;
+// Sites of one handle, all runs: 2^34 sites take 320 GB in the smallest storage
+// (D1Q5, FP16, two arenas), beyond the device; the bound keeps the host's tile
+// lists (int32 indices) and the planning within range before any allocation.
+constexpr int64_t kMaxTotalSites = (int64_t)1 << 34;
 
 struct GraphEntry {
   int64_t n, phase;
@@ -131,6 +135,27 @@ int cuda_fail(lb_ks* h, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                     \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
   } while (0)
+
+// No C++ exception crosses the C ABI: the entry points that allocate host memory catch
+// whatever escapes and call this from the handler, which turns the exception being
+// handled into a status (host allocation failure: LB_KS_ENOMEM) and a message.
+int abi_exception(lb_ks* h) noexcept {
+  int code = LB_KS_ECUDA;
+  const char* msg = "internal error: unexpected C++ exception";
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    code = LB_KS_ENOMEM;
+    msg = "host allocation failed";
+  } catch (...) {
+  }
+  try {
+    if (h) h->err = msg;
+    else g_ctor_error = msg;
+  } catch (...) {
+  }
+  return code;
+}
 
 // Device memory of the handles comes from one stream-ordered pool per device, created
 // on first use, which keeps up to kPoolKeep bytes reserved once they are freed: a
@@ -666,9 +691,11 @@ void warn_if_linearly_unstable(lb_ks* h, const double* L, const double* dt, cons
              ": growth rate " + std::to_string(worst) + " per unit time > 1.05 x 1/4)";
 }
 
-int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const double* L, const double* dt,
-           const double* tau, const double* rho0, const lb_ks_opts* opts, const double* rho_left = nullptr,
-           const double* rho_right = nullptr) {
+// The constructor.  h holds the handle while it is being built, so that the caller can
+// release it if an exception escapes; bail() releases it on a failed status.
+int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const double* L,
+                const double* dt, const double* tau, const double* rho0, const lb_ks_opts* opts,
+                const double* rho_left, const double* rho_right) {
   if (!out) return fail(nullptr, LB_KS_EINVAL, "h must not be NULL");
   *out = nullptr;
   const bool reservoir = rho_left != nullptr;
@@ -701,6 +728,8 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     if (o.kernel == LB_KS_KERNEL_COLLAPSE && tau[r] != 1.0)
       return fail(nullptr, LB_KS_EINVAL, "run " + std::to_string(r) + ": the collapse kernel needs tau = 1");
     total += N[r];
+    if (total > kMaxTotalSites)
+      return fail(nullptr, LB_KS_EINVAL, "the runs hold more than 2^34 sites in all (more than device memory holds)");
   }
   int ndev = 0;
   cudaError_t ce = cudaGetDeviceCount(&ndev);
@@ -709,11 +738,13 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
     return fail(nullptr, LB_KS_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
   }
 
-  lb_ks* h = new (std::nothrow) lb_ks();
+  h = new (std::nothrow) lb_ks();
   if (!h) return fail(nullptr, LB_KS_ENOMEM, "host allocation failed");
   auto bail = [&](int rc) {
     g_ctor_error = h->err;
-    lb_ks_free(h);
+    lb_ks* dead = h;
+    h = nullptr;
+    lb_ks_free(dead);
     return rc;
   };
   h->Q = scheme;
@@ -925,6 +956,20 @@ int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const dou
   return LB_KS_OK;
 }
 
+int create(lb_ks_t** out, int scheme, int32_t nruns, const int64_t* N, const double* L, const double* dt,
+           const double* tau, const double* rho0, const lb_ks_opts* opts, const double* rho_left = nullptr,
+           const double* rho_right = nullptr) {
+  lb_ks* h = nullptr;
+  try {
+    return create_body(h, out, scheme, nruns, N, L, dt, tau, rho0, opts, rho_left, rho_right);
+  } catch (...) {
+    const int rc = abi_exception(nullptr);
+    if (h) lb_ks_free(h);
+    if (out) *out = nullptr;
+    return rc;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -953,15 +998,18 @@ int lb_ks_batch_init(lb_ks_t** h, int scheme, int32_t nruns, const int64_t* N, c
 
 int lb_ks_batch_init_reservoir(lb_ks_t** h, int scheme, int32_t nruns, const int64_t* N, const double* L,
                                const double* dt, const double* tau, const double* rho0, const double* rho_left,
-                               const double* rho_right, const lb_ks_opts* opts) {
+                               const double* rho_right, const lb_ks_opts* opts) try {
   if (!rho_left || !rho_right) {
     if (h) *h = nullptr;
     return fail(nullptr, LB_KS_EINVAL, "rho_left and rho_right must not be NULL");
   }
   return create(h, scheme, nruns, N, L, dt, tau, rho0, opts, rho_left, rho_right);
+} catch (...) {
+  if (h) *h = nullptr;
+  return abi_exception(nullptr);
 }
 
-int lb_ks_step(lb_ks_t* h, int64_t n) {
+int lb_ks_step(lb_ks_t* h, int64_t n) try {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   if (h->sticky) return h->sticky;
   if (n < 0) return fail(h, LB_KS_EINVAL, "n must be >= 0");
@@ -982,9 +1030,23 @@ int lb_ks_step(lb_ks_t* h, int64_t n) {
     n -= c;
   }
   return LB_KS_OK;
+} catch (...) {
+  // the host's step counters may be ahead of what was issued: the handle is unusable
+  const int rc = abi_exception(h);
+  if (h) {
+    h->sticky = rc;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (h->cap_stream && cudaStreamIsCapturing(h->cap_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(h->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+  }
+  return rc;
 }
 
-int lb_ks_rho(lb_ks_t* h, double* out) {
+int lb_ks_rho(lb_ks_t* h, double* out) try {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   if (h->sticky) return h->sticky;
   if (!out) return fail(h, LB_KS_EINVAL, "out must not be NULL");
@@ -1010,9 +1072,11 @@ int lb_ks_rho(lb_ks_t* h, double* out) {
               "copy rho");
   LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   return check_flags(h);
+} catch (...) {
+  return abi_exception(h);
 }
 
-int lb_ks_mass_energy(lb_ks_t* h, double* mass, double* energy) {
+int lb_ks_mass_energy(lb_ks_t* h, double* mass, double* energy) try {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   if (h->sticky) return h->sticky;
   int64_t nk = 0;
@@ -1026,6 +1090,8 @@ int lb_ks_mass_energy(lb_ks_t* h, double* mass, double* energy) {
   if (mass) std::memcpy(mass, m.data(), sizeof(double) * h->nruns);
   if (energy) std::memcpy(energy, e.data(), sizeof(double) * h->nruns);
   return check_flags(h);
+} catch (...) {
+  return abi_exception(h);
 }
 
 int lb_ks_state_bytes(const lb_ks_t* h, size_t* bytes) {
@@ -1035,7 +1101,7 @@ int lb_ks_state_bytes(const lb_ks_t* h, size_t* bytes) {
   return LB_KS_OK;
 }
 
-int lb_ks_save(lb_ks_t* h, void* buf, size_t bytes) {
+int lb_ks_save(lb_ks_t* h, void* buf, size_t bytes) try {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   if (h->sticky) return h->sticky;
   size_t need = 0;
@@ -1059,9 +1125,11 @@ int lb_ks_save(lb_ks_t* h, void* buf, size_t bytes) {
                                cudaMemcpyDeviceToHost, h->stream), "save");
   LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   return check_flags(h);
+} catch (...) {
+  return abi_exception(h);
 }
 
-int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
+int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) try {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   size_t need = 0;
   lb_ks_state_bytes(h, &need);
@@ -1110,6 +1178,8 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) {
   h->sticky = LB_KS_OK;
   LBKS_CUDA(h, cudaMemset(h->d_flags, 0, sizeof(int)), "clear flags");
   return LB_KS_OK;
+} catch (...) {
+  return abi_exception(h);
 }
 
 int64_t lb_ks_steps_done(const lb_ks_t* h) { return h ? h->steps_done : -1; }
@@ -1170,7 +1240,7 @@ void lb_ks_free(lb_ks_t* h) {
 
 const char* lb_ks_last_error(const lb_ks_t* h) { return h ? h->err.c_str() : g_ctor_error.c_str(); }
 
-int lb_ks_fma_peak(int fp64, double* flops_per_s) {
+int lb_ks_fma_peak(int fp64, double* flops_per_s) try {
   if (!flops_per_s) return LB_KS_EINVAL;
   cudaError_t e = fma_peak(fp64, flops_per_s, nullptr);
   if (e != cudaSuccess) {
@@ -1178,6 +1248,8 @@ int lb_ks_fma_peak(int fp64, double* flops_per_s) {
     return LB_KS_ECUDA;
   }
   return LB_KS_OK;
+} catch (...) {
+  return abi_exception(nullptr);
 }
 
 }  // extern "C"

@@ -128,6 +128,21 @@ def test_reservoir_init_rejects_invalid_arguments(lb, bad):
     assert e.value.code == -1
 
 
+@pytest.mark.parametrize("Ns", [[(1 << 30) + 1], [1 << 30] * 17])
+def test_size_limits_are_einval(lb, Ns):
+    """A lattice above 2^30 sites, or more than 2^34 sites in all, is EINVAL before
+    any device or host work on the lattices (rho0 is not read: a one-value buffer
+    stands for it here)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("kept to machines where nothing could read past the one-value rho0")
+    n = len(Ns)
+    with pytest.raises(lb.LbKsError) as e:
+        lb.lb_ks_batch_init(7, Ns, np.full(n, 1e8), np.full(n, 1e-4), np.full(n, 1.5), np.zeros(1))
+    assert e.value.code == -1
+    assert "2^3" in lb.lb_ks_last_error(None)
+
+
 def test_no_device_is_an_error_not_a_fallback(lb):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
