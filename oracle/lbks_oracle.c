@@ -157,6 +157,8 @@ static int make_scheme(int Q, double alpha, double beta, double tau, int dm_vari
     if (g_mutation == 3) s->K = 0.0;  /* planted: drop the K w2 term */
     if (g_mutation == 4) s->J = -s->J; /* planted: wrong sign of the advection term */
     if (g_mutation == 5) s->E = 0.0;  /* planted: drop delta f^eq */
+    if (g_mutation == 6) s->M = 0.0;  /* planted: drop the M w4 term */
+    if (g_mutation == 7) s->dM = 0.0; /* planted: drop delta M */
     return LBO_OK;
 }
 
@@ -166,6 +168,13 @@ static void equilibrium(const scheme_t *s, double rho, double *feq) {
     for (int i = 0; i < s->Q; ++i) {
         double lin;
         const double *w1 = s->full_weights ? WF1 : W1;
+        double w1_swapped[7];
+        if (g_mutation == 9) { /* planted: the w1 entries of c = +2 and c = -2 exchanged */
+            for (int j = 0; j < s->Q; ++j) w1_swapped[j] = w1[j];
+            w1_swapped[3] = w1[4];
+            w1_swapped[4] = w1[3];
+            w1 = w1_swapped;
+        }
         const double *w2 = s->full_weights ? WF2 : W2;
         const double *w4 = s->full_weights ? WF4 : W4;
         if (s->Q == 5)
@@ -202,6 +211,7 @@ static void step_periodic(const scheme_t *s, int64_t N, const double *f, double 
         for (int i = 0; i < s->Q; ++i) {
             double fi = f[(int64_t)i * N + x];
             double fstar = fi - (fi - feq[i]) / s->tau;
+            if (g_mutation == 8) fstar = fi - (fi - feq[i]) * s->tau; /* planted: relaxed by tau, not 1/tau */
             int ci = g_mutation == 1 ? -c[i] : c[i]; /* planted: streaming direction flipped */
             fn[(int64_t)i * N + wrap(x + ci, N)] = fstar;
         }
@@ -232,6 +242,7 @@ static void step_reservoir(const scheme_t *s, int64_t Ne, const double *f, doubl
         for (int i = 0; i < s->Q; ++i) {
             double fi = f[(int64_t)i * Ne + x];
             double fstar = fi - (fi - feq[i]) / s->tau;
+            if (g_mutation == 8) fstar = fi - (fi - feq[i]) * s->tau; /* planted: relaxed by tau, not 1/tau */
             int64_t y = x + (g_mutation == 1 ? -c[i] : c[i]);
             if (y >= 0 && y < Ne) fn[(int64_t)i * Ne + y] = fstar;
         }

@@ -42,3 +42,55 @@ def test_dispersion_catches_dropped_delta_feq():
         bad = analysis.growth_rate(7, alpha, beta, tau, k, precise=True) - exact
     assert abs(good) < 3 * abs(e6) * k ** 6
     assert abs(bad) > 20 * abs(e6) * k ** 6
+
+
+def test_growth_rate_catches_dropped_m_term():
+    """Without M w4 the hyperdiffusion -k^4 of KS is gone from the growth rate."""
+    k = 0.5
+    good = analysis.growth_rate(5, 0.1, 1e-6, 1.0, k)
+    with lbks.mutation(6):
+        bad = analysis.growth_rate(5, 0.1, 1e-6, 1.0, k)
+    exact = k * k - k ** 4
+    assert abs(good - exact) < 1e-3 and abs(bad - exact - k ** 4) < 1e-3
+
+
+def test_dispersion_catches_dropped_delta_m():
+    """delta M exists to cancel the beta d^4 error of Eq. KS_trunc2: without it the
+    D1Q7 growth rate carries D1Q5's beta k^4 error term again."""
+    alpha, beta, tau = 0.1, 1e-4, 1.5
+    _, e6 = analysis.predicted_error_coefficients(7, alpha, beta, tau)
+    e4_q5, _ = analysis.predicted_error_coefficients(5, alpha, beta, tau)
+    k = 0.2
+    exact = k * k - k ** 4
+    good = analysis.growth_rate(7, alpha, beta, tau, k, precise=True) - exact
+    with lbks.mutation(7):
+        bad = analysis.growth_rate(7, alpha, beta, tau, k, precise=True) - exact
+    assert abs(good) < 3 * abs(e6) * k ** 6
+    assert abs(bad) > 8 * abs(e6) * k ** 6
+    assert abs(bad - e4_q5 * k ** 4) < 0.2 * abs(e4_q5 * k ** 4)
+
+
+@pytest.mark.parametrize("Q,tau", [(5, 1.7), (7, 2.5)])
+def test_matrix_power_catches_relaxation_by_tau(Q, tau):
+    """Relaxing by tau instead of 1/tau (the same at tau = 1, so the pin runs at
+    tau != 1): the step no longer follows the amplification matrix built with 1/tau."""
+    N, m, n = 64, 3, 400
+    alpha, beta = 0.2, 1e-4
+    kappa = 2 * np.pi * m / N
+    x = np.arange(N)
+    eps = 1e-2
+    expect = eps * np.real(analysis.linear_evolution(Q, alpha, beta, tau, kappa, n) * np.exp(1j * kappa * x))
+    good = lbks.run(Q, eps * np.cos(kappa * x), alpha, beta, tau, n, advection=False)
+    with lbks.mutation(8):
+        bad = lbks.run(Q, eps * np.cos(kappa * x), alpha, beta, tau, n, advection=False)
+    assert np.max(np.abs(good - expect)) < 1e-13
+    assert not np.all(np.abs(bad - expect) < 1e-6)
+
+
+def test_front_catches_exchanged_w1_entries():
+    """w1 with its c = +2 and c = -2 entries exchanged has first moment 5/3, not 1:
+    the advection, and so the front's speed, is wrong."""
+    good = _front_G(5)
+    with lbks.mutation(9):
+        bad = _front_G(5)
+    assert good < 2e-3 and bad > 20 * good
