@@ -182,6 +182,7 @@ static void equilibrium(const scheme_t *s, double rho, double *feq) {
         else
             lin = W0[i] + s->K * w2[i] + (s->M + s->dM) * w4[i] + s->E * W6[i];
         feq[i] = rho * lin + rho * rho * s->J * w1[i];
+        if (g_mutation == 10) feq[i] = rho * lin + rho * s->J * w1[i]; /* planted: linear advection term */
     }
 }
 

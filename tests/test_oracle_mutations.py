@@ -94,3 +94,13 @@ def test_front_catches_exchanged_w1_entries():
     with lbks.mutation(9):
         bad = _front_G(5)
     assert good < 2e-3 and bad > 20 * good
+
+
+@pytest.mark.parametrize("Q", [5, 7])
+def test_front_catches_linear_advection(Q):
+    """rho J w1 in place of rho^2 J w1 makes the advection of KS linear; the travelling
+    front of Table 5 exists only through that nonlinearity."""
+    good = _front_G(Q)
+    with lbks.mutation(10):
+        bad = _front_G(Q)
+    assert good < 2e-3 and bad > 50 * good
