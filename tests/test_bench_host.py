@@ -1,6 +1,7 @@
-"""CPU test of bench.py's reference arm (the FP64 oracle timed on the host cores):
-it prints one JSON line with the contract's keys, on the default arm's metric,
-unit and workload, and under torchrun only rank 0 runs and prints."""
+"""CPU tests of bench.py: the reference arm (the FP64 oracle timed on the host
+cores) prints one JSON line with the contract's keys, on the default arm's metric,
+unit and workload, and under torchrun only rank 0 runs and prints; the clock
+record of the timed region is read correctly from nvidia-smi's csv."""
 import json
 import os
 import subprocess
@@ -40,3 +41,33 @@ def test_reference_arm_other_ranks_exit_without_work():
                "--steps", "1", "--warmup", "3")
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_clock_sampler_reads_median_clock_and_active_reasons():
+    """The clock record of the timed region: median SM clock over the samples, the
+    maximum clock, and every throttle reason reported Active (csv, no units)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class FinishedProcess:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs.proc = FinishedProcess()
+    cs.lines = [
+        "2070, 2070, 901.25, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "1965, 2070, 1391.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 1203.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",  # a sample the driver could not read
+        "",
+    ]
+    r = cs.stop()
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
+    assert r["reasons"] == ["sw_power_cap"]
+    cs.lines = ["1400, 2070, 1000.0, 0x0000000000000008, Active, Not Active, Active, Not Active"]
+    r = cs.stop()
+    assert r["sm_mhz"] == 1400.0 and r["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
