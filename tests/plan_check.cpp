@@ -4,7 +4,8 @@
 // (c_max, sites per thread, threads per block, blocks per work group of whole
 // lattices, steps between halo exchanges of halves (0: none), steps per segment launch,
 // 1 to put single-block bundles two to a pair) and prints one line per case:
-//     OK rings=<pieces> halves=<lattices> spans=<rings across a pair> segs=<pieces> blocks=<groups> pairs=<groups>
+//     OK rings=<pieces> halves=<lattices> spans=<rings across a pair> segs=<pieces> blocks=<groups>
+//        pairs=<groups> segblocks=<groups> ring_threads=<threads> seg_threads=<threads>
 // or FAIL <reason>.  The line "FIRSTFIT <trials> <seed>" compares the groups' first
 // fit with a linear scan of the groups on random pieces.
 #include <cstdio>
@@ -129,13 +130,17 @@ std::string run_case(int C, int S, int NT, int cl, int kx, int kseg, int merge, 
   if (merged) check(pairs.members.size() == npair + (nsingle + 1) / 2, "single-block groups not two to a pair");
   if (!fail_.empty()) return "FAIL " + fail_;
   int halves = 0, spans = 0;
+  int64_t ring_threads = 0, seg_threads = 0;
   for (const Piece& p : rings) {
     halves += p.halo > 0 ? 1 : 0;
     spans += p.nthr > NT ? 1 : 0;
+    ring_threads += p.nthr;
   }
+  for (const Piece& p : segs) seg_threads += p.nthr;
   std::ostringstream o;
   o << "OK rings=" << rings.size() << " halves=" << halves / 2 << " spans=" << spans << " segs=" << segs.size()
-    << " blocks=" << blocks.members.size() << " pairs=" << pairs.members.size();
+    << " blocks=" << blocks.members.size() << " pairs=" << pairs.members.size() << " segblocks=" << segbins.members.size()
+    << " ring_threads=" << ring_threads << " seg_threads=" << seg_threads;
   return o.str();
 }
 

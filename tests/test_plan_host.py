@@ -46,22 +46,35 @@ def _kseg(C, S, NT):
     return max(1, NT * S // (20 * C))
 
 
+# (sites per thread, threads per block) of the resident kernel's tilings
+TILINGS = ((12, 384), (8, 256), (16, 256), (6, 512), (4, 1024))
+
+
 def test_benchmark_ensemble_plans(checker):
     from paper_1711_03540_gb300 import workloads
 
     Ns = workloads.ensemble(4096).N
     lines = []
-    for S, NT in ((12, 384), (8, 256), (16, 256), (6, 512), (4, 1024)):
+    for S, NT in TILINGS:
         for merge in (0, 1):
             lines.append(_line(3, S, NT, 2, 32, _kseg(3, S, NT), merge, Ns))
     lines.append(_line(3, 12, 384, 1, 0, _kseg(3, 12, 384), 0, Ns))  # one-block groups: long runs segmented
     lines.append(_line(3, 12, 384, 2, 16, _kseg(3, 12, 384), 1, Ns))
     res = checker(lines)
-    # 12 x 384: one block holds 4608 sites; every longer lattice is halved
+    # 12 x 384: one block holds 4608 sites; every longer lattice is halved, and the
+    # merged queue holds 1094 pair bundles (the benchmark's plan)
     assert int(res[1]["halves"]) == int((Ns > 12 * 384).sum()) == 687
-    assert int(res[1]["blocks"]) == 0 and int(res[1]["segs"]) == 0
+    assert int(res[1]["blocks"]) == 0 and int(res[1]["segs"]) == 0 and int(res[1]["pairs"]) == 1094
     assert int(res[0]["blocks"]) > 0  # unmerged: single-block bundles keep their own queue
     assert int(res[10]["pairs"]) == 0 and int(res[10]["segs"]) > 0
+    # packing: the groups' threads are mostly busy (rings 95-97 % with pairs, 99.5 %
+    # with single blocks; a segment gets a block of its own)
+    for j, d in enumerate(res):
+        NT = TILINGS[j // 2][1] if j < 2 * len(TILINGS) else 384
+        cap = (int(d["blocks"]) + 2 * int(d["pairs"])) * NT
+        assert int(d["ring_threads"]) / cap > (0.98 if j == 10 else 0.94)
+        if int(d["segblocks"]):
+            assert int(d["seg_threads"]) / (int(d["segblocks"]) * NT) > 0.75
 
 
 def test_edge_lengths(checker):
