@@ -48,9 +48,11 @@ void check_coverage(const std::vector<int64_t>& Ns, const std::vector<Piece>& al
   }
   for (size_t r = 0; r < Ns.size(); ++r)
     for (int64_t x = 0; x < Ns[r]; ++x)
-      if (!check(hits[r][(size_t)x] == 1, "run " + std::to_string(r) + " site " + std::to_string(x) + " stored " +
-                                              std::to_string(hits[r][(size_t)x]) + " times"))
+      if (hits[r][(size_t)x] != 1) {
+        check(false, "run " + std::to_string(r) + " site " + std::to_string(x) + " stored " +
+                         std::to_string(hits[r][(size_t)x]) + " times");
         return;
+      }
 }
 
 // Groups: thread ranges of their pieces inside the group and disjoint; in pair groups a
