@@ -2,8 +2,12 @@
  * gcc -std=c11 -pedantic -Werror against include/lb_ks.h: the header is valid C
  * and the entry points are callable from C.  Prints one "OK ..." line per check,
  * or "FAIL ..." and exits 1.  Without a usable device the constructors must
- * return LB_KS_ECUDA (no CPU fallback); with one, a short run is made. */
+ * return LB_KS_ECUDA (no CPU fallback); with one, a short run is made.
+ * "abi_check layout" instead prints, as "name value" lines, the size and field
+ * offsets of lb_ks_opts and the header's constants, for comparison with the
+ * Python binding. */
 #include <math.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -16,7 +20,48 @@ static void check(int ok, const char *what) {
     if (!ok) failures++;
 }
 
-int main(void) {
+static int print_layout(void) {
+#define FIELD(f) printf("offset_%s %zu\n", #f, offsetof(lb_ks_opts, f))
+    printf("sizeof_opts %zu\n", sizeof(lb_ks_opts));
+    FIELD(precision);
+    FIELD(dm_variant);
+    FIELD(recentre_every);
+    FIELD(kernel);
+    FIELD(steps_per_launch);
+    FIELD(sites_per_thread);
+    FIELD(threads_per_block);
+    FIELD(use_graph);
+    FIELD(autotune);
+    FIELD(stream);
+    FIELD(cluster_size);
+#undef FIELD
+#define CONST(c) printf("%s %d\n", #c, (int)(c))
+    CONST(LB_KS_OK);
+    CONST(LB_KS_EINVAL);
+    CONST(LB_KS_ENOMEM);
+    CONST(LB_KS_ECUDA);
+    CONST(LB_KS_EUNSTABLE);
+    CONST(LB_KS_ETIMEOUT);
+    CONST(LB_KS_D1Q5);
+    CONST(LB_KS_D1Q7);
+    CONST(LB_KS_F64);
+    CONST(LB_KS_F32);
+    CONST(LB_KS_F16S);
+    CONST(LB_KS_KERNEL_AUTO);
+    CONST(LB_KS_KERNEL_PLAIN);
+    CONST(LB_KS_KERNEL_STREAM);
+    CONST(LB_KS_KERNEL_RESIDENT);
+    CONST(LB_KS_KERNEL_COLLAPSE);
+    CONST(LB_KS_DM_DERIVED);
+    CONST(LB_KS_DM_PRINTED);
+    CONST(LB_KS_WEIGHTS_FULL_INVERSE);
+    CONST(LB_KS_LANE_FIELDS);
+#undef CONST
+    return 0;
+}
+
+int main(int argc, char **argv) {
+    if (argc > 1 && strcmp(argv[1], "layout") == 0) return print_layout();
     lb_ks_opts o;
     memset(&o, 0xff, sizeof o);
     lb_ks_default_opts(&o);
