@@ -1,6 +1,7 @@
 """CPU tests of the C ABI: the library loads and exports every entry point
-declared in include/lb_ks.h, the host-side precompute matches the oracle,
-and argument validation fails cleanly (no GPU needed)."""
+declared in include/lb_ks.h, the binding's prototypes match the header's, the
+host-side precompute matches the oracle, and argument validation fails cleanly
+(no GPU needed)."""
 import math
 import os
 import re
@@ -174,3 +175,42 @@ def test_max_growth_classifies_as_the_oracle_around_the_critical_step(lb):
         assert lb.lb_ks_max_growth(Q, dx, 1.1 * dtc, tau) > 1.05 * 0.25
     with pytest.raises(lb.LbKsError):
         lb.lb_ks_max_growth(7, 0.1, 1e-4, 1.5, nk=0)
+
+
+def _c_kind(t: str):
+    """Kind and width of a C parameter or return type of lb_ks.h."""
+    t = " ".join(t.replace("const", " ").split())
+    if "*" in t:
+        return "ptr"
+    return {"void": None, "int": "i32", "int32_t": "i32", "int64_t": "i64", "double": "f64", "size_t": "u64"}[t]
+
+
+def _ctypes_kind(t):
+    import ctypes as C
+
+    if t is None:
+        return None
+    if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+        return "ptr"
+    if t is C.c_double:
+        return "f64"
+    if t is C.c_size_t:
+        return "u64"
+    return {4: "i32", 8: "i64"}[C.sizeof(t)]
+
+
+def test_binding_prototypes_match_header(lb):
+    """Every ctypes prototype of the binding has the header's return type and, parameter
+    by parameter, the same kind and width (pointers as pointers)."""
+    txt = re.sub(r"/\*.*?\*/", " ", open(os.path.join(ROOT, "include", "lb_ks.h")).read(), flags=re.S)
+    protos = re.findall(r"LB_KS_API\s+([^;(]*?)\b(lb_ks_\w+)\s*\(([^)]*)\)\s*;", txt)
+    assert len(protos) == len(lb.ABI_FUNCTIONS)
+    for ret, name, params in protos:
+        restype, argtypes = lb.ABI_FUNCTIONS[name]
+        assert _ctypes_kind(restype) == _c_kind(ret), name
+        c_params = []
+        for prm in params.split(","):
+            prm = " ".join(prm.split())
+            typ = prm if "*" in prm else prm.rsplit(" ", 1)[0]  # drop the parameter's name
+            c_params.append(_c_kind(typ))
+        assert [_ctypes_kind(a) for a in argtypes] == c_params, name
