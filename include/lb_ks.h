@@ -26,7 +26,9 @@
  *    cudaPointerGetAttributes.
  *  - Work is issued on the stream given in lb_ks_opts (NULL = the legacy
  *    default stream).  lb_ks_step returns without waiting; lb_ks_rho,
- *    lb_ks_mass_energy and lb_ks_save wait for the stream.
+ *    lb_ks_mass_energy and lb_ks_save wait for the stream.  The stream must
+ *    outlive the handle: lb_ks_free waits for it and returns the handle's
+ *    device memory to the pool in its order.
  *  - Errors detected on the device (a non-finite FP64 mass at a guard step)
  *    are sticky: they are reported by the next call that waits, and every
  *    later call on the handle returns the same code.
