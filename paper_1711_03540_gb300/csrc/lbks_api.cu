@@ -32,6 +32,7 @@ constexpr int kPlainTile = 256;
 constexpr int kAlign = 32;  // elements: run offsets and the plane stride are multiples of this
 constexpr uint32_t kMagic = 0x534b424cu;  // "LBKS"
 constexpr uint32_t kVersion = 1;
+
 // Sites of one handle, all runs: 2^34 sites take 320 GB in the smallest storage
 // (D1Q5, FP16, two arenas), beyond the device; the bound keeps the host's tile
 // lists (int32 indices) and the planning within range before any allocation.
@@ -232,8 +233,8 @@ bool valid_opts(const lb_ks_opts& o, std::string* why) {
   if (o.kernel == LB_KS_KERNEL_COLLAPSE && o.precision == LB_KS_F16S) { *why = "the tau = 1 collapse stores F64 or F32"; return false; }
   if (o.steps_per_launch < 0) { *why = "opts.steps_per_launch must be >= 0"; return false; }
   if (o.sites_per_thread != 0 && o.sites_per_thread != 4 && o.sites_per_thread != 6 && o.sites_per_thread != 8 &&
-      o.sites_per_thread != 12 && o.sites_per_thread != 16 && o.sites_per_thread != 32) {
-    *why = "opts.sites_per_thread must be 0, 4, 6, 8, 12, 16 or 32"; return false;
+      o.sites_per_thread != 12 && o.sites_per_thread != 16 && o.sites_per_thread != 18 && o.sites_per_thread != 32) {
+    *why = "opts.sites_per_thread must be 0, 4, 6, 8, 12, 16, 18 or 32"; return false;
   }
   if (o.threads_per_block != 0 && (o.threads_per_block < 32 || o.threads_per_block > 512 || o.threads_per_block % 32)) {
     *why = "opts.threads_per_block must be 0 or a multiple of 32 in [32, 512]"; return false;
@@ -588,7 +589,7 @@ int autotune_resident(lb_ks* h) {
   } else if (h->prec == kF64) {
     tilings = {{8, 256}, {6, 256}, {4, 256}};
   } else {
-    tilings = {{12, 384}, {16, 256}, {8, 512}};
+    tilings = {{18, 256}, {12, 384}, {16, 256}, {8, 512}};
   }
   for (auto& tl : tilings) {
     const int NT = tl.second ? tl.second : (col ? 256 : default_threads(h->prec, tl.first));

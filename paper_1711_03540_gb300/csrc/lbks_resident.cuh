@@ -32,21 +32,28 @@
 // carries link code only for bundles that need it (resident_steps<LINK>).
 //
 // One step of Eq. LB_equation_ordinary:
-//  A. per held site: s_g = sum_i g_i, rho = rhobar + s_g, rho^2;
+//  A. per held site: s_g = sum_i g_i, rho = rhobar + s_g, rho^2; g_0's register takes
+//     s_g, from which phase B subtracts each plane's post-collision value (the same
+//     arithmetic, in the same order, as collide(): g_0 = s_g - sum_{i>=1} g*_i);
 //  B. per plane i >= 1, the post-collision value of every site is written
 //     straight into the register of the site it streams to (c_i > 0: sites
 //     visited from the last one down, c_i < 0: from the first one up, so the
-//     destination register's old value has already been used); the c_i values
-//     that leave the thread go to shared memory;  g_0 = s_g - sum of the others
-//     (mass conservation; the same arithmetic, in the same order, as collide());
+//     destination register's old value has already been used); the values at the
+//     thread's edge go to its column of the exchange area: for speed +k the last k + 1
+//     slots, for -k the first k + 1 (one more than leave a thread holding S sites);
 //  (a ring across a cluster pair: after A, the two threads at the block edge push
-//     the values that leave the block this step, computed from A's sums;)
+//     the same k + 1 values per plane, computed from A's sums, into the other block;)
 //  C. one block barrier (and, for the two threads of a cluster block with a link
 //     across the block edge, the mbarrier wait), then the values entering from
 //     the neighbour thread are read (the neighbour of a piece's last thread is
 //     its first: periodic wrap).  The exchange area is double-buffered by step
 //     parity, so one barrier per step orders both the reads after the writes
 //     and the next overwrite after the reads.
+// Threads holding S - 1 sites (slots 0..S-2; slot S-1 holds a bounded value that no
+// site reads) take the same code path: with k + 1 values stored per plane and side,
+// a reader finds the k values it needs one row further in or not (per thread, fixed
+// for the bundle: its left neighbour holds S sites, or it holds S - 1 itself), so the
+// only extra work of an (S - 1)-site thread is one predicated load per -k plane.
 // For a segment the wrap injects unrelated values at its two ends; they travel
 // at most c_max sites per step and never reach the stored middle.
 //
@@ -71,6 +78,11 @@ namespace lbks {
 namespace {
 
 template <int ST, int S> struct ResidentCfg {
+  // Threads without a piece skip the step's arithmetic (S <= 12), or step zeros in their
+  // own exchange column (S > 12: the loop without the two branches schedules better there;
+  // measured on uniform lattices, 16 x 256: 8.9e11 -> 9.9e11 site-updates/s, while at
+  // 12 x 384, 168 registers, the branches are worth 8 %).
+  static constexpr bool kSkipIdle = S <= 12;
   // Upper bound of threads per block; sets the register budget per thread.
   static constexpr int kMaxThreads = (ST == kF64) ? 256 : (S <= 8 ? 512 : (S <= 12 ? 384 : 256));
   // Row length of the exchange area: a column per thread of the largest block and two
@@ -106,14 +118,18 @@ constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before a wait is g
 
 // Dynamic shared memory (elements): the staging area of the launch edges
 // [Q planes][NT threads x S sites], then the exchange area
-// [2 parities][2 directions][NX][XS] (XS = ResidentCfg::kXS): a column per thread for
+// [2 parities][2 directions][xrows][XS] (XS = ResidentCfg::kXS): a column per thread for
 // the values leaving it, and the last two (XS - 2: right-moving, XS - 1: left-moving)
 // for the values the other block of a cluster pushes in, then the inbox of a lattice half
 // [2 parities][2 sides][Q][c_max kPairStepsMax]: side 0 the other half's last halo
 // sites (this half's left halo), side 1 its first ones (the right halo).  Neither
 // overlaps the staging area, since the other block may write them while this block
 // is still staging.
-__host__ __device__ constexpr int exchange_rows(int Q) { return 4 * ((Q - 1) / 2) * ((Q - 1) / 2 + 1) / 2; }
+// Rows of one direction of the exchange area: k + 1 for the plane of speed k = 1..c_max,
+// from row xrow(k).
+__host__ __device__ constexpr int xrows(int C) { return C * (C + 3) / 2; }
+__host__ __device__ constexpr int xrow(int k) { return k * (k + 1) / 2 - 1; }
+__host__ __device__ constexpr int exchange_rows(int Q) { return 4 * xrows((Q - 1) / 2); }
 __host__ __device__ constexpr int halo_max(int Q) { return ((Q - 1) / 2) * kPairStepsMax; }
 __host__ __device__ constexpr size_t smem_elems(int Q, int S, int NT, int XS) {
   return (size_t)Q * S * NT + (size_t)exchange_rows(Q) * XS + (size_t)4 * Q * halo_max(Q);
@@ -153,6 +169,12 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
 }
 __device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+// Barrier `id` over the first `count` arrivals (a multiple of 32: whole warps), with the
+// memory ordering of __syncthreads among the threads that take part (PTX ISA: bar.sync).
+__device__ __forceinline__ void named_barrier(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // ---- mbarriers with transaction counts (PTX ISA: mbarrier, st.async)
@@ -195,44 +217,42 @@ __device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar)
 }
 
 // Edge values of one thread for the other block of a cluster: the post-collision
-// values that leave the thread to the right (c_i > 0: sites n - c_i .. n - 1 of its
-// n held sites) or to the left (c_i < 0: sites 0 .. |c_i| - 1), from the
-// pre-collision populations f and phase A's rho and rho^2, with the operations of
-// phase B (which computes the same values again below), stored into the other
-// block's pushed-in column (element stride ntx, row |c|(|c|-1)/2 + j).
-template <int Q, int n, typename CT, int SF>
-__device__ __forceinline__ void push_edge_right(const CT (&f)[Q][SF], const CT (&rho)[SF], const CT (&rho2)[SF],
+// values of its last k + 1 slots for each speed +k (push_edge_right) or of its first
+// k + 1 for each -k (push_edge_left), from the pre-collision populations f and phase
+// A's rho and rho^2, with the operations of phase B (which computes the same values
+// again below), stored into the other block's pushed-in column (element stride ntx,
+// the rows of phase B's own column).
+template <int Q, typename CT, int S>
+__device__ __forceinline__ void push_edge_right(const CT (&f)[Q][S], const CT (&rho)[S], const CT (&rho2)[S],
                                                 const Coef<CT, Q>& k, uint32_t col, int ntx, uint32_t mbar) {
   StaticFor<1, Q>::run([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     constexpr int c = speed(i);
     if constexpr (c > 0) {
-      constexpr int base = c * (c - 1) / 2;
 #pragma unroll
-      for (int j = 0; j < c; ++j) {
-        constexpr int s0 = n - c;
+      for (int j = 0; j <= c; ++j) {
+        constexpr int s0 = S - 1 - c;
         const CT v = post_collision(k.r, f[i][s0 + j], rho[s0 + j], rho2[s0 + j], k.b[i], mul_rn(rho[s0 + j], k.a[i]));
-        st_async(col + (uint32_t)((base + j) * ntx * sizeof(CT)), v, mbar);
+        st_async(col + (uint32_t)((xrow(c) + j) * ntx * sizeof(CT)), v, mbar);
       }
     }
   });
 }
 
-template <int Q, typename CT, int SF>
-__device__ __forceinline__ void push_edge_left(const CT (&f)[Q][SF], const CT (&rho)[SF], const CT (&rho2)[SF],
+template <int Q, typename CT, int S>
+__device__ __forceinline__ void push_edge_left(const CT (&f)[Q][S], const CT (&rho)[S], const CT (&rho2)[S],
                                                const Coef<CT, Q>& k, uint32_t col, int ntx, uint32_t mbar) {
   StaticFor<1, Q>::run([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     constexpr int c = speed(i);
     if constexpr (c < 0) {
       constexpr int kk = -c;
-      constexpr int base = kk * (kk - 1) / 2;
 #pragma unroll
-      for (int j = 0; j < kk; ++j) {
+      for (int j = 0; j <= kk; ++j) {
         // phase B takes rho a_i of the -c plane from the +c plane before it (a_i is even in
         // c) and b_i as minus that plane's (b_i is odd in c, exactly)
         const CT v = post_collision(k.r, f[i][j], rho[j], rho2[j], -k.b[i - 1], mul_rn(rho[j], k.a[i - 1]));
-        st_async(col + (uint32_t)((base + j) * ntx * sizeof(CT)), v, mbar);
+        st_async(col + (uint32_t)((xrow(kk) + j) * ntx * sizeof(CT)), v, mbar);
       }
     }
   });
@@ -256,70 +276,76 @@ struct ClusterLink {
 // LINK: the bundle has a piece across the edge of a cluster pair, whose boundary
 // values go through the other block's shared memory; without it the loop is that of
 // a single block (no link code in the loop, so no registers or instructions spent on it).
-template <int Q, int S, int XS, bool LINK, typename CT>
+// lt, rt: exchange columns of the left and right neighbours; lfull: the left neighbour
+// holds S sites; full: this thread does.  SKIP (see ResidentCfg::kSkipIdle): threads
+// without a piece skip the arithmetic and every thread takes part in the block barrier.
+// Otherwise, without LINK, warps without a piece leave at once (wrun false) and the step
+// barrier is the named barrier 1 over the nbar threads of the warps that hold one; with
+// LINK every thread steps (those without a piece on zeros), so that every thread keeps
+// the link's phase parities.
+template <int Q, int S, int XS, bool LINK, bool SKIP, typename CT>
 __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>& k, const int step0, const int ksteps,
-                                               CT* const xbase, const int NT, const int t, const bool active,
-                                               const bool full, const int lt, const int rt, ClusterLink& ln) {
+                                               CT* const xbase, const int t, const bool active, const bool full,
+                                               const int lt, const int rt, const bool lfull, const bool wrun,
+                                               const int nbar, ClusterLink& ln) {
+  constexpr bool kLeave = !SKIP && !LINK;
+  if (kLeave && !wrun) return;
   constexpr int C = cmax_of(Q);
-  constexpr int NX = C * (C + 1) / 2;  // values leaving a thread per direction per step
+  constexpr int NR = xrows(C);  // rows per direction
   constexpr int NTX = XS;
+  // Where this thread reads: the right-moving values of its left neighbour's column, one
+  // row in when that neighbour holds S sites (its row 0 is a value that stays inside it);
+  // the left-moving values of its right neighbour's column, one row in when this thread
+  // holds S - 1 sites (row 0 then goes to slot S - 1 - k, the others to S - k .. S - 1).
+  const int rd_r = (lfull ? NTX : 0) + lt;
+  const int rd_l = (NR + (full ? 0 : 1)) * NTX + rt;
   for (int step = step0; step < step0 + ksteps; ++step) {
     const int pb = step & 1;
-    const int par = pb * 2 * NX * NTX;
-    CT* const xr = xbase + par;  // right-moving values leaving threads
-    CT* const xl = xr + NX * NTX; // left-moving values leaving threads
+    CT* const xp = xbase + pb * 2 * NR * NTX;  // this step's exchange area: [R|L][NR][NTX]
+    CT* const xw = xp + t;                     // this thread's column
     if constexpr (LINK) {
       // this step's phase of ln.mbar[pb] completes on this arrival and on the
-      // 2 NX values the other block pushes (NX per direction)
-      if (ln.lrem && !ln.bad) mbar_arrive_expect_tx(&ln.mbar[pb], 2 * NX * (uint32_t)sizeof(CT));
+      // 2 NR values the other block pushes (NR per direction)
+      if (ln.lrem && !ln.bad) mbar_arrive_expect_tx(&ln.mbar[pb], 2 * NR * (uint32_t)sizeof(CT));
     }
-    if (active) {
-      // A. per-site sums
-      CT acc[S], rho[S], rho2[S], tt[S];
+    if (!SKIP || active) {
+      // A. per-site sums; g_0's register becomes the accumulator of g*_0
+      CT rho[S], rho2[S], tt[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         CT sg = f[0][s];
 #pragma unroll
         for (int i = 1; i < Q; ++i) sg = add_rn(sg, f[i][s]);
-        acc[s] = sg;
         rho[s] = add_rn(k.rhobar, sg);
         rho2[s] = mul_rn(rho[s], rho[s]);
+        f[0][s] = sg;
       }
       if constexpr (LINK) {
         // Push the values this step sends across the block edge before phase B, from
         // phase A's sums with the arithmetic of phase B (which computes them again
         // below), so that the transfer overlaps the rest of the step.
-        if (ln.rrem) {
-          const uint32_t col = ln.peer_x + (uint32_t)((par + XS - 2) * sizeof(CT));
-          if (full) push_edge_right<Q, S>(f, rho, rho2, k, col, NTX, ln.peer_mbar + 8u * pb);
-          else push_edge_right<Q, S - 1>(f, rho, rho2, k, col, NTX, ln.peer_mbar + 8u * pb);
-        }
+        if (ln.rrem)
+          push_edge_right<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)((pb * 2 * NR * NTX + XS - 2) * sizeof(CT)), NTX,
+                             ln.peer_mbar + 8u * pb);
         if (ln.lrem)
-          push_edge_left<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)((par + NX * NTX + XS - 1) * sizeof(CT)), NTX,
-                            ln.peer_mbar + 8u * pb);
+          push_edge_left<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)(((pb * 2 + 1) * NR * NTX + XS - 1) * sizeof(CT)),
+                            NTX, ln.peer_mbar + 8u * pb);
       }
-      // B. plane by plane: collide, write to the destination site's register or send.
+      // B. plane by plane: collide, write to the destination site's register and/or the
+      // exchange column.
       StaticFor<1, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int c = speed(i);
         constexpr int kk = c > 0 ? c : -c;
-        constexpr int base = kk * (kk - 1) / 2;
+        constexpr int row0 = xrow(kk);
         if constexpr (c > 0) {
 #pragma unroll
           for (int s = S - 1; s >= 0; --s) {
             tt[s] = mul_rn(rho[s], k.a[i]);  // shared with the -c plane that follows
             const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], k.b[i], tt[s]);
-            acc[s] = add_rn(acc[s], -v);
-            if (s + kk <= S - 2) {
-              f[i][s + kk] = v;
-            } else if (s + kk == S - 1) {
-              if (full) f[i][S - 1] = v;
-              else xr[base * NTX + t] = v;
-            } else if (s <= S - 2) {
-              xr[(base + (full ? s + kk - S : s + kk - S + 1)) * NTX + t] = v;
-            } else if (full) {  // s == S - 1 holds a site only in threads with S sites
-              xr[(base + s + kk - S) * NTX + t] = v;
-            }
+            f[0][s] = add_rn(f[0][s], -v);
+            if (s >= S - 1 - kk) xw[(row0 + s - (S - 1 - kk)) * NTX] = v;
+            if (s + kk <= S - 1) f[i][s + kk] = v;
           }
         } else {
 #pragma unroll
@@ -327,16 +353,15 @@ __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>&
             // b_i of the -c plane is exactly minus the +c plane's (B_i = J w1_i, w1 odd in
             // c), taken with the FMA's negation so that it needs no register of its own
             const CT v = post_collision(k.r, f[i][s], rho[s], rho2[s], -k.b[i - 1], tt[s]);
-            acc[s] = add_rn(acc[s], -v);
+            f[0][s] = add_rn(f[0][s], -v);
+            if (s <= kk) xw[(NR + row0 + s) * NTX] = v;
             if (s >= kk) f[i][s - kk] = v;
-            else xl[(base + s) * NTX + t] = v;
           }
         }
       });
-#pragma unroll
-      for (int s = 0; s < S; ++s) f[0][s] = acc[s];
     }
-    __syncthreads();
+    if constexpr (kLeave) named_barrier(1, nbar);
+    else __syncthreads();
     if constexpr (LINK) {
       if ((ln.lrem || ln.rrem) && !ln.bad) {
         uint32_t it = 0;
@@ -350,26 +375,21 @@ __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>&
       }
       ln.ph ^= 1u << pb;
     }
-    if (active) {
+    if (!SKIP || active) {
       // C. values entering from the neighbours (pushed in by the other block for
       // a piece's threads at a block edge)
       StaticFor<1, Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int c = speed(i);
         constexpr int kk = c > 0 ? c : -c;
-        constexpr int base = kk * (kk - 1) / 2;
+        constexpr int row0 = xrow(kk);
         if constexpr (c > 0) {
 #pragma unroll
-          for (int jj = 0; jj < kk; ++jj)
-            f[i][jj] = xr[(base + jj) * NTX + lt];
+          for (int jj = 0; jj < kk; ++jj) f[i][jj] = xp[rd_r + (row0 + jj) * NTX];
         } else {
-          // threads with S sites fill slots S-kk .. S-1, threads with S-1 sites S-1-kk .. S-2
 #pragma unroll
-          for (int jj = 0; jj < kk; ++jj) {
-            const CT v = xl[(base + jj) * NTX + rt];
-            if (full) f[i][S - kk + jj] = v;
-            else f[i][S - 1 - kk + jj] = v;
-          }
+          for (int jj = 0; jj < kk; ++jj) f[i][S - kk + jj] = xp[rd_l + (row0 + jj) * NTX];
+          if (!full) f[i][S - 1 - kk] = xp[rd_l + (row0 - 1) * NTX];
         }
       });
     }
@@ -483,13 +503,12 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
   static_assert(CL == 1 || CL == 2, "work groups are one block or a pair of blocks");
   using T = typename StorageType<ST>::type;
   using CT = typename StorageType<ST>::compute;
-  constexpr int C = cmax_of(Q);
-  constexpr int NX = C * (C + 1) / 2;  // values leaving a thread per direction per step
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NT = blockDim.x;
   constexpr int NTX = ResidentCfg<ST, S>::kXS;        // exchange-area row length
+  constexpr bool kSkip = ResidentCfg<ST, S>::kSkipIdle;
   CT* const stage = reinterpret_cast<CT*>(smem_raw);   // [Q][NT * S] at the launch edges
-  CT* const xbase = stage + Q * S * NT;                // [parity][R|L][NX][NTX]
+  CT* const xbase = stage + Q * S * NT;                // [parity][R|L][xrows][NTX]
   CT* const inbox = xbase + exchange_rows(Q) * NTX;    // [parity][L|R halo][Q][c_max kPairStepsMax]
   __shared__ int s_bundle;
   __shared__ int s_half[3];                            // CL = 2: halo, own sites, threads of this block's half
@@ -549,10 +568,11 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
     }
 
     CT f[Q][S];
-    Coef<CT, Q> k;
+    Coef<CT, Q> k{};
     bool full = true;
     int start = 0;
     int lt = t, rt = t;                    // exchange columns the incoming values are read from
+    bool lfull = true;                     // the left neighbour holds S sites
     bool lrem = false, rrem = false;       // left / right neighbour in the other block
     PieceGeom G{};
     const T* fs = nullptr;
@@ -572,6 +592,7 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       rrem = rrank != rank;
       lt = lrem ? NTX - 2 : lg - lrank * NT;   // pushed-in columns for a neighbour in the other block
       rt = rrem ? NTX - 1 : rg - rrank * NT;
+      lfull = (j == 0 ? V - 1 : j - 1) < pc.n - V * (S - 1);
       fs = static_cast<const T*>(a.src.f) + d.off;
     }
 
@@ -592,6 +613,12 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       for (int i = 0; i < Q; ++i)
 #pragma unroll
         for (int s = 0; s < S; ++s) f[i][s] = (s < S - 1 || full) ? stage[i * NT * S + G.sbase + start + s] : CT(0);
+    } else {
+      // a thread without a piece steps zeros in its own exchange column
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int s = 0; s < S; ++s) f[i][s] = CT(0);
     }
     // block-uniform: does a piece of this bundle span both blocks (then this block
     // has one thread with lrem and one with rrem, possibly the same thread)
@@ -600,9 +627,10 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       span = __syncthreads_or(lrem || rrem);
       // block-uniform: the bundle holds a lattice as two halves (one per block)
       halves = __syncthreads_or(active && a.pieces[pidx].halo > 0);
-    } else {
-      __syncthreads();
     }
+    // the warps that hold a piece, and their threads (the step barrier's count)
+    const bool wrun = __any_sync(0xffffffffu, active);
+    const int nbar = 32 * __syncthreads_count(wrun && (t & 31) == 0);
 
     ClusterLink ln;
     if constexpr (CL == 2) {
@@ -615,7 +643,7 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
         ln.rrem = rrem;
         ln.bad = s_bad != 0;
         ln.flags = a.flags;
-        resident_steps<Q, S, NTX, true>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
+        resident_steps<Q, S, NTX, true, kSkip>(f, k, 0, a.ksteps, xbase, t, active, full, lt, rt, lfull, wrun, nbar, ln);
         // every thread toggled the same parities; the next write follows the barriers
         // of the store phase below
         if (t == 0) s_ph = ln.ph;
@@ -623,15 +651,15 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
       } else if (halves && a.kx > 0) {
         for (int s0 = 0; s0 < a.ksteps; s0 += a.kx) {
           const int kk = min(a.kx, a.ksteps - s0);
-          resident_steps<Q, S, NTX, false>(f, k, s0, kk, xbase, NT, t, active, full, lt, rt, ln);
+          resident_steps<Q, S, NTX, false, kSkip>(f, k, s0, kk, xbase, t, active, full, lt, rt, lfull, wrun, nbar, ln);
           if (s0 + kk < a.ksteps)
             halo_exchange<Q, S>(f, s_half, full, start, NT, t, stage, inbox, (s0 / a.kx) & 1);
         }
       } else {
-        resident_steps<Q, S, NTX, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
+        resident_steps<Q, S, NTX, false, kSkip>(f, k, 0, a.ksteps, xbase, t, active, full, lt, rt, lfull, wrun, nbar, ln);
       }
     } else {
-      resident_steps<Q, S, NTX, false>(f, k, 0, a.ksteps, xbase, NT, t, active, full, lt, rt, ln);
+      resident_steps<Q, S, NTX, false, kSkip>(f, k, 0, a.ksteps, xbase, t, active, full, lt, rt, lfull, wrun, nbar, ln);
     }
     __syncthreads();
 
@@ -681,6 +709,7 @@ size_t smem_bytes_t(int NT) {
       case 8: { constexpr int Sc = 8; OP; }                                           \
       case 12: if constexpr (STc != kF64) { constexpr int Sc = 12; OP; } break;       \
       case 16: if constexpr (STc != kF64) { constexpr int Sc = 16; OP; } break;       \
+      case 18: if constexpr (STc != kF64) { constexpr int Sc = 18; OP; } break;       \
       default: break;                                                                 \
     }                                                                                 \
   }
