@@ -340,6 +340,21 @@ LB_KS_API int lb_ks_fma_peak(int fp64, double *flops_per_s);
 LB_KS_API int lb_ks_mass_energy_noalloc(int scheme, int precision, const void *f, int64_t plane, int64_t N,
                                         double rhobar, double scale, double *out, void *stream);
 
+/* Testing aid for the link between the two blocks of a cluster pair (no counterpart
+ * in the paper).  A lattice held as one ring across both blocks of a pair sends, every
+ * step, the values that cross the block edge into the other block's shared memory, and
+ * the receiving threads wait for them with a bounded wait.  With withhold_step >= 0,
+ * block 1 of every pair sends nothing across the edge at that step of each launch
+ * (counted from the launch's first step), so that the receiving wait in block 0 runs
+ * out; wait_rounds is the number of try_wait rounds before a wait gives up (0: the
+ * default, 2^22).  A wait that runs out is reported by the next call that checks the
+ * handle's status as LB_KS_ETIMEOUT, which then sticks; the launch itself completes.
+ * Only bundles with such a ring are affected (the plan's halves and single blocks
+ * never wait on the other block).  Call before the first lb_ks_step (LB_KS_EINVAL
+ * afterwards: captured step sequences keep the values they were captured with).
+ * Errors: LB_KS_EINVAL (NULL handle, withhold_step < -1, called after a step). */
+LB_KS_API int lb_ks_set_link_test(lb_ks_t *h, int32_t withhold_step, uint32_t wait_rounds);
+
 /* Release the handle and its device memory.  NULL is ignored. */
 LB_KS_API void lb_ks_free(lb_ks_t *h);
 

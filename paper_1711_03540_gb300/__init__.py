@@ -23,7 +23,7 @@ __all__ = [
     "LbKsError", "LbKsOpts", "lb_ks_default_opts", "lb_ks_params", "lb_ks_tau_fit", "lb_ks_init",
     "lb_ks_batch_init", "lb_ks_batch_init_reservoir", "lb_ks_step", "lb_ks_rho", "lb_ks_mass_energy", "lb_ks_state_bytes", "lb_ks_save",
     "lb_ks_load", "lb_ks_steps_done", "lb_ks_describe", "lb_ks_launches", "lb_ks_fma_peak",
-    "lb_ks_mass_energy_noalloc", "lb_ks_free",
+    "lb_ks_mass_energy_noalloc", "lb_ks_set_link_test", "lb_ks_free",
     "lb_ks_last_error", "library_path", "D1Q5", "D1Q7", "F64", "F32", "F16S", "KERNEL_AUTO", "KERNEL_PLAIN",
     "KERNEL_STREAM", "KERNEL_RESIDENT", "ABI_FUNCTIONS",
 ]
@@ -82,6 +82,7 @@ ABI_FUNCTIONS = {
     "lb_ks_fma_peak": (C.c_int, [C.c_int, _PD]),
     "lb_ks_mass_energy_noalloc": (C.c_int, [C.c_int, C.c_int, _P, C.c_int64, C.c_int64, C.c_double, C.c_double, _P,
                                             _P]),
+    "lb_ks_set_link_test": (C.c_int, [_P, C.c_int32, C.c_uint32]),
     "lb_ks_free": (None, [_P]),
     "lb_ks_last_error": (C.c_char_p, [_P]),
 }
@@ -264,6 +265,11 @@ def lb_ks_mass_energy_noalloc(scheme: int, precision: int, f, plane: int, N: int
     rc = _load().lb_ks_mass_energy_noalloc(scheme, precision, _ptr(f, None), int(plane), int(N), float(rhobar),
                                            float(scale), _ptr(out), C.c_void_p(int(s) if s else 0))
     _check(rc)
+
+
+def lb_ks_set_link_test(h, withhold_step: int, wait_rounds: int = 0) -> None:
+    """Testing aid: withhold block 1's sends across a cluster pair's edge at one step."""
+    _check(_load().lb_ks_set_link_test(h, int(withhold_step), int(wait_rounds)), h)
 
 
 def lb_ks_free(h) -> None:

@@ -113,6 +113,8 @@ struct lb_ks {
   int64_t steps_done = 0;
   int64_t phase = 0;  // steps since the last guard
   int64_t launches = 0;
+  uint32_t link_wait_limit = 1u << 22;  // lb_ks_set_link_test
+  int link_withhold_step = -1;
   int sticky = LB_KS_OK;
   std::string err = "no error";
   std::vector<GraphEntry> graphs;
@@ -421,7 +423,7 @@ int issue_lane(lb_ks* h, const Lane& L, int64_t k, int from, bool in_place, cuda
     LBKS_CUDA(h, cudaMemsetAsync(L.d_queue, 0, sizeof(int), s), "queue reset");
     ResidentLaunch RL{h->Q, h->prec, h->S, h->NT, arena(h, cur), arena(h, dst), h->d_runs,
                       L.d_pieces, L.d_bundles, L.nbundles, L.d_queue, (int)kk, L.grid, L.cl, h->d_flags,
-                      h->nplanes == 1, L.kx};
+                      h->nplanes == 1, L.kx, h->link_wait_limit, h->link_withhold_step};
     LBKS_CUDA(h, launch_resident(RL, s), "resident step");
     *nk += 1;
     cur = dst;
@@ -1184,6 +1186,16 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) try {
 }
 
 int64_t lb_ks_steps_done(const lb_ks_t* h) { return h ? h->steps_done : -1; }
+
+int lb_ks_set_link_test(lb_ks_t* h, int32_t withhold_step, uint32_t wait_rounds) {
+  if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
+  if (withhold_step < -1) return fail(h, LB_KS_EINVAL, "withhold_step must be >= -1");
+  if (h->steps_done != 0 || !h->graphs.empty())
+    return fail(h, LB_KS_EINVAL, "lb_ks_set_link_test must be called before the first lb_ks_step");
+  h->link_withhold_step = withhold_step;
+  h->link_wait_limit = wait_rounds ? wait_rounds : (1u << 22);
+  return LB_KS_OK;
+}
 
 int lb_ks_describe(const lb_ks_t* h, int* kernel, int* spt, int* tpb, int* spl, int* cl, int32_t* nruns,
                    int64_t* total) {

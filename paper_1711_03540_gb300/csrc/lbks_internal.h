@@ -112,6 +112,8 @@ struct ResidentLaunch {
   int* flags = nullptr;  // error flags (bit 2: a bounded wait between the blocks of a cluster ran out)
   bool collapse = false;  // the tau = 1 collapse (one stored plane) instead of the LB populations
   int kx = 0;             // cl = 2: steps between the halo exchanges of lattice halves (Piece::halo)
+  uint32_t wait_limit = 1u << 22;  // cl = 2: try_wait rounds before a wait on the other block gives up
+  int withhold_step = -1;          // cl = 2, testing aid: block 1 sends nothing across the edge at this step
 };
 bool resident_supported(int Q, int storage, int S, int NT);
 cudaError_t resident_prepare(int Q, int storage, int S, int NT, int* blocks_per_sm);

@@ -37,7 +37,7 @@ cudaError_t prepare_t(int NT, int* max_clusters) {
 
 template <int Q, int ST, int S>
 cudaError_t launch_t(const ResidentLaunch& L, cudaStream_t s) {
-  const ResidentArgs a{L.src, L.dst, L.runs, L.pieces, L.bundles, L.nbundles, L.queue, L.ksteps, L.flags, L.kx};
+  const ResidentArgs a{L.src, L.dst, L.runs, L.pieces, L.bundles, L.nbundles, L.queue, L.ksteps, L.flags, L.kx, L.wait_limit, L.withhold_step};
   cudaLaunchAttribute attr;
   const cudaLaunchConfig_t cfg = cluster_config<Q, ST, S>(L.grid, L.NT, s, &attr);
   return cudaLaunchKernelEx(&cfg, resident_kernel<Q, ST, S, 2>, a);

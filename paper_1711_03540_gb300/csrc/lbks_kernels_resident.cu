@@ -20,7 +20,7 @@ cudaError_t prepare_t(int NT, int* blocks_per_sm) {
 
 template <int Q, int ST, int S>
 cudaError_t launch_t(const ResidentLaunch& L, cudaStream_t s) {
-  ResidentArgs a{L.src, L.dst, L.runs, L.pieces, L.bundles, L.nbundles, L.queue, L.ksteps, L.flags, L.kx};
+  ResidentArgs a{L.src, L.dst, L.runs, L.pieces, L.bundles, L.nbundles, L.queue, L.ksteps, L.flags, L.kx, L.wait_limit, L.withhold_step};
   resident_kernel<Q, ST, S, 1><<<L.grid, L.NT, smem_bytes_t<Q, ST, S>(L.NT), s>>>(a);
   return cudaGetLastError();
 }

@@ -20,13 +20,18 @@
 //    it has exactly two links across the block edge (block 0's last thread <->
 //    block 1's first, and its own periodic wrap), so each block has one thread that
 //    receives right-moving values from the other block and one that receives
-//    left-moving values.  Those threads push their outgoing values into the other
-//    block's shared memory with st.async, whose completion counts bytes on an
-//    mbarrier there; the receiving thread waits on its own block's mbarrier (a
-//    bounded wait: on time-out it sets an error flag, stops waiting and the launch
-//    completes).  Each link is used in both directions every step, so a push into a
-//    double-buffered slot is always ordered after the reads of that slot two steps
-//    earlier.  The rest of the step uses __syncthreads only.
+//    left-moving values.  The threads that send them store their outgoing values
+//    into the other block's shared memory (plain st.shared::cluster) and then arrive
+//    on that block's mbarrier with release semantics at cluster scope (two arrivals
+//    complete a phase); the receiving threads wait on their own block's mbarrier with
+//    acquire semantics (a bounded wait: on time-out it sets an error flag, the block
+//    stops waiting for the rest of the launch and the launch completes).  Each link
+//    is used in both directions every step, so a store into a double-buffered slot is
+//    always ordered after the reads of that slot two steps earlier.  The rest of the
+//    step uses block barriers only.  Every remote write is an ordinary store that
+//    precedes its thread's next cluster barrier, so none can still be in flight when
+//    the blocks pass the cluster barriers between bundles or before they exit, also
+//    after a time-out, when the receiving side no longer waits.
 // A pair's spare threads hold whole small lattices, and a pair may also run two
 // single-block bundles side by side (no piece across the edge); the step loop
 // carries link code only for bundles that need it (resident_steps<LINK>).
@@ -111,10 +116,12 @@ struct ResidentArgs {
   int ksteps;
   int* flags;  // bit 2 set when a bounded wait on the other block of a cluster ran out
   int kx;      // cluster pairs: steps between the halo exchanges of lattice halves
+  uint32_t wait_limit;  // try_wait rounds before a wait on the other block is given up
+  int withhold_step;    // testing aid: block 1 of a pair sends nothing across the edge
+                        // at this step of every bundle with a ring across both blocks (-1: none)
 };
 
 constexpr int kFlagClusterTimeout = 2;
-constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before a wait is given up
 
 // Dynamic shared memory (elements): the staging area of the launch edges
 // [Q planes][NT threads x S sites], then the exchange area
@@ -177,7 +184,7 @@ __device__ __forceinline__ void named_barrier(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// ---- mbarriers with transaction counts (PTX ISA: mbarrier, st.async)
+// ---- mbarriers (PTX ISA: mbarrier)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -185,16 +192,18 @@ __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
 }
 
-// Makes the initialised mbarriers visible to the other blocks of the cluster
-// (complete_tx from there); a cluster barrier follows before any use.
+// Makes the initialised mbarriers visible to the other blocks of the cluster (which
+// arrive on them); a cluster barrier follows before any use.
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+// Arrive on the mbarrier at cluster address `mbar` (in another block of the cluster),
+// releasing this thread's earlier stores at cluster scope.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 // One bounded round of waiting for the completion of phase `parity`; acquire at
-// cluster scope, so the bytes that st.async from the other block wrote are visible.
+// cluster scope, so the values the other block stored before its arrivals are visible.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -205,26 +214,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity) {
   return ok != 0;
 }
 
-// Store v at addr in another block's shared memory; its completion counts
-// sizeof(v) bytes on the mbarrier at mbar (in that block).
-__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t mbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];"
-               ::"r"(addr), "f"(v), "r"(mbar) : "memory");
-}
-__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];"
-               ::"r"(addr), "d"(v), "r"(mbar) : "memory");
-}
-
 // Edge values of one thread for the other block of a cluster: the post-collision
 // values of its last k + 1 slots for each speed +k (push_edge_right) or of its first
 // k + 1 for each -k (push_edge_left), from the pre-collision populations f and phase
 // A's rho and rho^2, with the operations of phase B (which computes the same values
-// again below), stored into the other block's pushed-in column (element stride ntx,
-// the rows of phase B's own column).
+// again below), stored into the other block's pushed-in column (cluster address col,
+// element stride ntx, the rows of phase B's own column).
 template <int Q, typename CT, int S>
 __device__ __forceinline__ void push_edge_right(const CT (&f)[Q][S], const CT (&rho)[S], const CT (&rho2)[S],
-                                                const Coef<CT, Q>& k, uint32_t col, int ntx, uint32_t mbar) {
+                                                const Coef<CT, Q>& k, uint32_t col, int ntx) {
   StaticFor<1, Q>::run([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     constexpr int c = speed(i);
@@ -233,7 +231,7 @@ __device__ __forceinline__ void push_edge_right(const CT (&f)[Q][S], const CT (&
       for (int j = 0; j <= c; ++j) {
         constexpr int s0 = S - 1 - c;
         const CT v = post_collision(k.r, f[i][s0 + j], rho[s0 + j], rho2[s0 + j], k.b[i], mul_rn(rho[s0 + j], k.a[i]));
-        st_async(col + (uint32_t)((xrow(c) + j) * ntx * sizeof(CT)), v, mbar);
+        st_cluster(col + (uint32_t)((xrow(c) + j) * ntx * sizeof(CT)), v);
       }
     }
   });
@@ -241,7 +239,7 @@ __device__ __forceinline__ void push_edge_right(const CT (&f)[Q][S], const CT (&
 
 template <int Q, typename CT, int S>
 __device__ __forceinline__ void push_edge_left(const CT (&f)[Q][S], const CT (&rho)[S], const CT (&rho2)[S],
-                                               const Coef<CT, Q>& k, uint32_t col, int ntx, uint32_t mbar) {
+                                               const Coef<CT, Q>& k, uint32_t col, int ntx) {
   StaticFor<1, Q>::run([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     constexpr int c = speed(i);
@@ -252,7 +250,7 @@ __device__ __forceinline__ void push_edge_left(const CT (&f)[Q][S], const CT (&r
         // phase B takes rho a_i of the -c plane from the +c plane before it (a_i is even in
         // c) and b_i as minus that plane's (b_i is odd in c, exactly)
         const CT v = post_collision(k.r, f[i][j], rho[j], rho2[j], -k.b[i - 1], mul_rn(rho[j], k.a[i - 1]));
-        st_async(col + (uint32_t)((xrow(kk) + j) * ntx * sizeof(CT)), v, mbar);
+        st_cluster(col + (uint32_t)((xrow(kk) + j) * ntx * sizeof(CT)), v);
       }
     }
   });
@@ -270,6 +268,8 @@ struct ClusterLink {
   bool rrem = false;  // the right neighbour is in the other block
   bool bad = false;   // a wait ran out: stop waiting (the flag tells the host)
   int* flags = nullptr;
+  uint32_t limit = 0;     // try_wait rounds before a wait is given up
+  int withhold = -1;      // testing aid: send nothing across the edge at this step
 };
 
 // ksteps steps of the register-resident state f (see the kernel below for phases A-C).
@@ -303,11 +303,6 @@ __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>&
     const int pb = step & 1;
     CT* const xp = xbase + pb * 2 * NR * NTX;  // this step's exchange area: [R|L][NR][NTX]
     CT* const xw = xp + t;                     // this thread's column
-    if constexpr (LINK) {
-      // this step's phase of ln.mbar[pb] completes on this arrival and on the
-      // 2 NR values the other block pushes (NR per direction)
-      if (ln.lrem && !ln.bad) mbar_arrive_expect_tx(&ln.mbar[pb], 2 * NR * (uint32_t)sizeof(CT));
-    }
     if (!SKIP || active) {
       // A. per-site sums; g_0's register becomes the accumulator of g*_0
       CT rho[S], rho2[S], tt[S];
@@ -321,15 +316,25 @@ __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>&
         f[0][s] = sg;
       }
       if constexpr (LINK) {
-        // Push the values this step sends across the block edge before phase B, from
+        // Send the values this step sends across the block edge before phase B, from
         // phase A's sums with the arithmetic of phase B (which computes them again
-        // below), so that the transfer overlaps the rest of the step.
-        if (ln.rrem)
-          push_edge_right<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)((pb * 2 * NR * NTX + XS - 2) * sizeof(CT)), NTX,
-                             ln.peer_mbar + 8u * pb);
-        if (ln.lrem)
-          push_edge_left<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)(((pb * 2 + 1) * NR * NTX + XS - 1) * sizeof(CT)),
-                            NTX, ln.peer_mbar + 8u * pb);
+        // below), so that the transfer overlaps the rest of the step; each sending
+        // thread then arrives on the other block's mbarrier of this parity, releasing its
+        // stores at cluster scope (this step's phase there completes on the two
+        // arrivals, one per direction).  Arriving after phase B instead delays the
+        // receiver: 7 % slower rings.
+        if (step != ln.withhold) {
+          if (ln.rrem) {
+            push_edge_right<Q>(f, rho, rho2, k, ln.peer_x + (uint32_t)((pb * 2 * NR * NTX + XS - 2) * sizeof(CT)),
+                               NTX);
+            mbar_arrive_remote(ln.peer_mbar + 8u * pb);
+          }
+          if (ln.lrem) {
+            push_edge_left<Q>(f, rho, rho2, k,
+                              ln.peer_x + (uint32_t)(((pb * 2 + 1) * NR * NTX + XS - 1) * sizeof(CT)), NTX);
+            mbar_arrive_remote(ln.peer_mbar + 8u * pb);
+          }
+        }
       }
       // B. plane by plane: collide, write to the destination site's register and/or the
       // exchange column.
@@ -366,7 +371,7 @@ __device__ __forceinline__ void resident_steps(CT (&f)[Q][S], const Coef<CT, Q>&
       if ((ln.lrem || ln.rrem) && !ln.bad) {
         uint32_t it = 0;
         while (!mbar_try_wait(&ln.mbar[pb], (ln.ph >> pb) & 1u)) {
-          if (++it == kWaitLimit) {
+          if (++it >= ln.limit) {
             ln.bad = true;
             if (ln.flags) atomicOr(ln.flags, kFlagClusterTimeout);
             break;
@@ -512,7 +517,7 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
   CT* const inbox = xbase + exchange_rows(Q) * NTX;    // [parity][L|R halo][Q][c_max kPairStepsMax]
   __shared__ int s_bundle;
   __shared__ int s_half[3];                            // CL = 2: halo, own sites, threads of this block's half
-  __shared__ __align__(8) uint64_t s_mbar[2];          // CL = 2: counts the pushed bytes, one per parity
+  __shared__ __align__(8) uint64_t s_mbar[2];          // CL = 2: the other block's sends, one per parity
   // CL = 2, kept in shared memory between the bundles whose pieces span the block edge
   // (so that no registers are held for them while other bundles run): bit p of s_ph is
   // the parity of the next phase of s_mbar[p] to complete; s_bad: a wait ran out, stop
@@ -524,8 +529,8 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
   const int g = rank * NT + t;  // thread index in the work group
   if constexpr (CL == 2) {
     if (t == 0) {
-      mbar_init(&s_mbar[0], 1);
-      mbar_init(&s_mbar[1], 1);
+      mbar_init(&s_mbar[0], 2);  // one arrival per direction from the other block
+      mbar_init(&s_mbar[1], 2);
       fence_mbar_init();
       s_ph = 0;
       s_bad = 0;
@@ -643,6 +648,8 @@ __global__ void __launch_bounds__(ResidentCfg<ST, S>::kMaxThreads, 1) resident_k
         ln.rrem = rrem;
         ln.bad = s_bad != 0;
         ln.flags = a.flags;
+        ln.limit = a.wait_limit;
+        ln.withhold = rank == 1 ? a.withhold_step : -1;
         resident_steps<Q, S, NTX, true, kSkip>(f, k, 0, a.ksteps, xbase, t, active, full, lt, rt, lfull, wrun, nbar, ln);
         // every thread toggled the same parities; the next write follows the barriers
         // of the store phase below

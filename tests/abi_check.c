@@ -119,7 +119,8 @@ int main(int argc, char **argv) {
     lb_ks_free(NULL);
     size_t bytes = 0;
     check(lb_ks_steps_done(NULL) == -1 && lb_ks_launches(NULL) == -1 && lb_ks_state_bytes(NULL, &bytes) == LB_KS_EINVAL &&
-              lb_ks_step(NULL, 1) == LB_KS_EINVAL && lb_ks_rho(NULL, rho) == LB_KS_EINVAL,
+              lb_ks_step(NULL, 1) == LB_KS_EINVAL && lb_ks_rho(NULL, rho) == LB_KS_EINVAL &&
+              lb_ks_set_link_test(NULL, 0, 16u) == LB_KS_EINVAL,
           "NULL handles");
     return failures ? 1 : 0;
 }

@@ -182,7 +182,8 @@ def _c_kind(t: str):
     t = " ".join(t.replace("const", " ").split())
     if "*" in t:
         return "ptr"
-    return {"void": None, "int": "i32", "int32_t": "i32", "int64_t": "i64", "double": "f64", "size_t": "u64"}[t]
+    return {"void": None, "int": "i32", "int32_t": "i32", "uint32_t": "u32", "int64_t": "i64", "double": "f64",
+            "size_t": "u64"}[t]
 
 
 def _ctypes_kind(t):
@@ -196,6 +197,8 @@ def _ctypes_kind(t):
         return "f64"
     if t is C.c_size_t:
         return "u64"
+    if t is C.c_uint32:
+        return "u32"
     return {4: "i32", 8: "i64"}[C.sizeof(t)]
 
 

@@ -244,3 +244,42 @@ def test_cluster_checkpoint_and_graph_replay(lb):
     np.testing.assert_array_equal(a, ref)
     np.testing.assert_array_equal(b, ref)
 
+
+
+def test_link_wait_that_runs_out_is_reported_and_the_device_stays_usable(lb):
+    """Failure detection of the link between the two blocks of a pair: a lattice of 400
+    sites at 4 sites x 64 threads runs as one ring across both blocks (halves with
+    their 96-site halos would not fit a block).  With the testing aid, block 1 sends
+    nothing across the edge at step 5 of each launch and a wait gives up after 4096
+    rounds, so block 0's wait for that step runs out: the launch completes, the next
+    call that checks the status reports LB_KS_ETIMEOUT, it sticks, the handle frees,
+    and a new handle on the same device computes the ring bitwise as before."""
+    Ns = np.array([400], dtype=np.int64)
+    r0, taus = _inputs(Ns, 91)
+    opts = dict(precision=1, kernel=3, sites_per_thread=4, threads_per_block=64, cluster_size=2)
+    ref, desc = run_gpu(lb, 7, Ns, r0, 40, taus, **opts)
+    assert desc["cluster_size"] == 2 and sum(ln["halved_lattices"] for ln in desc["lanes"]) == 0
+    h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(1, 1e-4), taus, r0, lb.lb_ks_default_opts(**opts))
+    try:
+        lb.lb_ks_set_link_test(h, 5, 4096)
+        lb.lb_ks_step(h, 40)
+        out = np.empty(400)
+        with pytest.raises(lb.LbKsError) as e:
+            lb.lb_ks_rho(h, out)
+        assert e.value.code == -5
+        with pytest.raises(lb.LbKsError) as e:
+            lb.lb_ks_step(h, 1)
+        assert e.value.code == -5
+    finally:
+        lb.lb_ks_free(h)
+    # the aid is refused once a handle has stepped
+    h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(1, 1e-4), taus, r0, lb.lb_ks_default_opts(**opts))
+    try:
+        lb.lb_ks_step(h, 1)
+        with pytest.raises(lb.LbKsError) as e:
+            lb.lb_ks_set_link_test(h, 5, 4096)
+        assert e.value.code == -1
+    finally:
+        lb.lb_ks_free(h)
+    again, _ = run_gpu(lb, 7, Ns, r0, 40, taus, **opts)
+    np.testing.assert_array_equal(again, ref)
