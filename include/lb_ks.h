@@ -323,19 +323,21 @@ LB_KS_API int lb_ks_fma_peak(int fp64, double *flops_per_s);
  *      double, float or __half for precision LB_KS_F64, LB_KS_F32, LB_KS_F16S
  *      (the populations section of a checkpoint written by lb_ks_save, run 0,
  *      has this layout).
- *   rho(x) = rhobar + scale * sum_i f_i(x)  (rhobar = 0, scale = 1 for FP64;
- *      for F32 / F16S the run's storage offset and scale).
+ *   rho(x) = rhobar + scale * sum_i f_i(x): rhobar = 0 for FP64, the run's storage
+ *      offset (its initial mean) for F32 and F16S; scale is the run's storage scale
+ *      for F16S and must be 1 for FP64 and F32 (other values: LB_KS_EINVAL).
  *   out: 2 doubles (mass, energy), host or device memory.
  * The partial sums live in one static device array of 256 KB (2 x 16384 + 2
  * doubles), present on every device that loads the library until exit; it
  * limits N to 2^24 sites (larger N: LB_KS_EINVAL).  The first call on a device
  * looks the array's address up (cudaGetSymbolAddress) and must be made with
  * that device current; make that first call before any stream capture on the
- * device.  All calls share the array: calls that overlap on the GPU (other
+ * device.  The address is kept for the life of the process: do not call this
+ * entry point on a device after cudaDeviceReset of that device.  All calls share the array: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Runs on stream (cudaStream_t, NULL = legacy default) and waits for it.
  * Errors: LB_KS_EINVAL (bad scheme/precision, NULL pointers, N < 1,
- * N > 2^24, plane < N, scale <= 0), LB_KS_ECUDA.
+ * N > 2^24, plane < N, scale <= 0, scale != 1 for FP64 or F32), LB_KS_ECUDA.
  */
 LB_KS_API int lb_ks_mass_energy_noalloc(int scheme, int precision, const void *f, int64_t plane, int64_t N,
                                         double rhobar, double scale, double *out, void *stream);

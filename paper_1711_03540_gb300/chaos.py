@@ -10,8 +10,9 @@ chaos; the statistics are those any KS study reports.
 
     python -m paper_1711_03540_gb300.chaos --steps 1000000 --burn-in 200000
 
-runs the 1024-run chaos ensemble in FP32 (with the FP64 guard) and in FP64 and
-prints one JSON line with both sets of statistics and their relative differences.
+runs the 1024-run chaos ensemble in FP32 and in scaled FP16 (with the FP64 guard)
+and in FP64 and prints one JSON line with the statistics and the relative
+differences of each reduced storage against FP64.
 """
 from __future__ import annotations
 
@@ -105,7 +106,7 @@ def compare(a: dict, b: dict, rel_floor: float = 0.01) -> dict:
 
 
 def main() -> None:
-    from . import F32, F64, build, workloads
+    from . import F16S, F32, F64, build, workloads
 
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--nruns", type=int, default=1024)
@@ -115,6 +116,7 @@ def main() -> None:
     build.build()
     wl = workloads.chaos_ensemble(nruns=args.nruns)
     s32 = ensemble_statistics(wl, F32, args.steps, args.burn_in)
+    s16 = ensemble_statistics(wl, F16S, args.steps, args.burn_in)
     s64 = ensemble_statistics(wl, F64, args.steps, args.burn_in)
     cmp = compare(s64, s32)
     line = {"workload": wl.name, "sites": int(wl.N.sum()), "steps": args.steps, "burn_in": args.burn_in,
@@ -123,7 +125,11 @@ def main() -> None:
                      "site_updates_per_s": s32["site_updates"] / s32["seconds"]},
             "fp64": {"mean_rho2": float(np.mean(s64["mean_rho2"])), "seconds": s64["seconds"],
                      "site_updates_per_s": s64["site_updates"] / s64["seconds"]},
+            "f16s": {"mean_rho2": float(np.mean(s16["mean_rho2"])), "seconds": s16["seconds"],
+                     "site_updates_per_s": s16["site_updates"] / s16["seconds"]},
             "fp32_vs_fp64": cmp,
+            "f16s_vs_fp64": compare(s64, s16),
+            "spectrum_f16s": [float(v) for v in s16["spectrum"]],
             "spectrum_fp64": [float(v) for v in s64["spectrum"]],
             "spectrum_fp32": [float(v) for v in s32["spectrum"]],
             "k_bins": [float(v) for v in K_BINS]}

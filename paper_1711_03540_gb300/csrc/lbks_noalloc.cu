@@ -76,7 +76,9 @@ __global__ void na_total_kernel(int ntiles, double* __restrict__ scratch) {
   }
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device, looked up once per device
+// and kept for the life of the process (it does not survive cudaDeviceReset of that
+// device, after which the module, and the array, are loaded anew).
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -103,6 +105,7 @@ extern "C" int lb_ks_mass_energy_noalloc(int scheme, int precision, const void* 
   if ((scheme != LB_KS_D1Q5 && scheme != LB_KS_D1Q7) || precision < LB_KS_F64 || precision > LB_KS_F16S)
     return LB_KS_EINVAL;
   if (!f || !out || N < 1 || plane < N || !(scale > 0.0)) return LB_KS_EINVAL;
+  if (precision != LB_KS_F16S && scale != 1.0) return LB_KS_EINVAL;  // only FP16 storage is scaled
   if (N > (int64_t)kNaTileSites * kNaMaxTiles) return LB_KS_EINVAL;  // beyond the static scratch
   double* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);

@@ -1,9 +1,9 @@
 """Long-time statistics of the chaotic D1Q7 ensemble (1024 runs, L ~ U(22, 200),
-Delta X log-uniform in [0.05, 0.1], tau = 3, Delta T = 1e-4): FP32 storage with the
-FP64 guard against FP64, by the ensemble-mean time-averaged <rho^2> and the
-time-averaged energy spectrum in wavenumber bins, each within 2 % (bins holding at
-least 1 % of the largest).  Trajectories of a chaotic system are compared by
-statistics, not point by point.  This test runs T = 30 with averages over
+Delta X log-uniform in [0.05, 0.1], tau = 3, Delta T = 1e-4): FP32 and scaled-FP16
+storage with the FP64 guard against FP64, by the ensemble-mean time-averaged <rho^2>
+and the time-averaged energy spectrum in wavenumber bins, each within 2 % (bins
+holding at least 1 % of the largest).  Trajectories of a chaotic system are compared
+by statistics, not point by point.  This test runs T = 30 with averages over
 T in (10, 30]; `python -m paper_1711_03540_gb300.chaos` runs the full T = 100
 with a T = 20 burn-in."""
 import numpy as np
@@ -25,16 +25,27 @@ def lb():
     return lb
 
 
-def test_fp32_statistics_match_fp64(lb):
+STEPS, BURN = 300_000, 100_000
+
+
+@pytest.fixture(scope="module")
+def fp64_statistics(lb):
     from paper_1711_03540_gb300 import chaos, workloads
 
     wl = workloads.chaos_ensemble(nruns=1024)
-    steps, burn = 300_000, 100_000
-    s64 = chaos.ensemble_statistics(wl, lb.F64, steps, burn)
-    s32 = chaos.ensemble_statistics(wl, lb.F32, steps, burn)
-    c = chaos.compare(s64, s32)
+    s64 = chaos.ensemble_statistics(wl, lb.F64, STEPS, BURN)
     assert s64["energy_samples"] == 200 and s64["spectrum_samples"] == 20
     assert np.all(np.isfinite(s64["mean_rho2"])) and np.mean(s64["mean_rho2"]) > 1e-3  # the runs are active
+    return wl, s64
+
+
+@pytest.mark.parametrize("prec", ["F32", "F16S"])
+def test_reduced_storage_statistics_match_fp64(lb, fp64_statistics, prec):
+    from paper_1711_03540_gb300 import chaos
+
+    wl, s64 = fp64_statistics
+    s = chaos.ensemble_statistics(wl, getattr(lb, prec), STEPS, BURN)
+    c = chaos.compare(s64, s)
     assert c["bins_compared"] >= 10
     assert c["mean_rho2_rel"] <= 0.02, c
     assert c["spectrum_max_rel"] <= 0.02, c

@@ -166,6 +166,34 @@ def test_fp32_error_against_oracle(lb, kern):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) <= bound
 
 
+@pytest.mark.parametrize("kern,kpl", [(3, 500), (3, 100), (2, 1)])
+def test_f16s_error_against_oracle(lb, kern, kpl):
+    """Scaled FP16 storage (FP32 arithmetic; populations stored as g / scale in FP16,
+    scale per lattice) against the FP64 oracle on the lattices of the FP32 test.  The
+    state is rounded to FP16 E times: once at initialisation, then at every launch
+    edge of the resident kernel (kpl steps per launch) or after every step of the
+    streaming kernel; each rounding moves a stored value by at most half an ulp,
+    2^-12 of it, so the error is bounded by a random walk of E Q roundings of ulp
+    2^-11, amplified at most by the largest KS growth rate 1/4:
+    sqrt(E Q) 2^-11 exp(T/4).  (The FP32 arithmetic adds sqrt(n Q) 2^-24.)"""
+    Ns = np.array([256, 1000, 4000, 8192], dtype=np.int64)
+    from paper_1711_03540_gb300 import workloads
+
+    rng = np.random.default_rng(5)
+    r0 = np.concatenate([workloads.random_modes(int(n), n * 0.1, rng) for n in Ns])
+    taus = np.array([1.5, 2.0, 2.5, 3.0])
+    n, dt = 2000, 1e-4
+    ref, _ = ora.run_batch(7, Ns, np.full(4, 0.1), np.full(4, dt), taus, r0, n)
+    out, _ = run_gpu(lb, 7, Ns, Ns * 0.1, dt, taus, r0, n, precision=2, kernel=kern, recentre_every=500,
+                     steps_per_launch=kpl if kern == 3 else 0)
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    E = 1 + (n // kpl)
+    bound = np.sqrt(E * 7) * 2.0 ** -11 * np.exp(n * dt / 4) + np.sqrt(n * 7) * 2.0 ** -24
+    for i in range(Ns.size):
+        a, b = out[off[i]:off[i + 1]], ref[off[i]:off[i + 1]]
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= bound, (Ns[i], bound)
+
+
 def test_printed_delta_m_variant_matches_oracle_and_differs(lb):
     """The printed reading of Eq. delta_M is kept as an option: the GPU follows the
     oracle with the same reading, and the two readings differ once tau != 1."""
