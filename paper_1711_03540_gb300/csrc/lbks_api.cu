@@ -321,7 +321,7 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
   else if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
   else if (col) cand = h->prec == kF64 ? std::vector<int>{16, 8} : std::vector<int>{32, 16, 8};
   else if (h->prec == kF64) cand = {8, 6, 4};
-  else cand = {12, 8, 16, 6, 4};
+  else cand = {18, 12, 8, 16, 6, 4};
   const int R = h->opts.recentre_every;
   for (int S : cand) {
     const int NT = NT_force ? NT_force

@@ -1,7 +1,8 @@
 // HBM-streaming fused step for large lattices (one launch per step).
 //
 // A block owns a tile of kTile consecutive sites of one run.  Each thread
-// loads kVec consecutive sites of every plane with one vector load, collides
+// loads VEC consecutive sites of every plane with one 16-byte load (4 sites of
+// FP32, 8 of FP16 with half as many threads per block; FP64: two loads), collides
 // them in registers and writes f* to a shared-memory copy of the tile that
 // also holds c_max post-collision halo sites on each side (computed by a few
 // threads from the neighbouring sites, periodic wrap).  After one barrier
@@ -18,31 +19,40 @@ namespace lbks {
 
 namespace {
 
-constexpr int kStreamThreads = 256;
-constexpr int kVec = 4;
-constexpr int kTile = kStreamThreads * kVec;  // 1024 sites
-constexpr int kHalo = 4;                      // >= c_max, keeps float4 stores aligned
+constexpr int kTile = 1024;  // sites per block (the host's streaming tiles)
+constexpr int kHalo = 4;     // >= c_max, keeps the vector stores aligned
 
-template <typename T> struct Vec4;
-template <> struct Vec4<float> {
-  static __device__ __forceinline__ void load(const float* p, float (&v)[kVec]) {
+// Sites per thread and threads per block of a storage type: 16-byte loads of each
+// plane (FP64 two of them), the same tile of kTile sites.
+template <int ST> struct StreamShape {
+  static constexpr int kVec = ST == kF16S ? 8 : 4;
+  static constexpr int kThreads = kTile / kVec;
+};
+
+template <typename T> struct VecLoad;
+template <> struct VecLoad<float> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
     const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   }
 };
-template <> struct Vec4<double> {
-  static __device__ __forceinline__ void load(const double* p, double (&v)[kVec]) {
+template <> struct VecLoad<double> {
+  static __device__ __forceinline__ void load(const double* p, double (&v)[4]) {
     const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
     const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
 };
-template <> struct Vec4<__half> {
-  static __device__ __forceinline__ void load(const __half* p, __half (&v)[kVec]) {
-    const uint2 q = __ldcs(reinterpret_cast<const uint2*>(p));
-    const __half2 a = *reinterpret_cast<const __half2*>(&q.x);
-    const __half2 b = *reinterpret_cast<const __half2*>(&q.y);
-    v[0] = __low2half(a); v[1] = __high2half(a); v[2] = __low2half(b); v[3] = __high2half(b);
+template <> struct VecLoad<__half> {
+  static __device__ __forceinline__ void load(const __half* p, __half (&v)[8]) {
+    const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __half2 a = *reinterpret_cast<const __half2*>(&w[j]);
+      v[2 * j] = __low2half(a);
+      v[2 * j + 1] = __high2half(a);
+    }
   }
 };
 
@@ -55,33 +65,42 @@ using TileType = typename std::conditional<ST == kF16S, typename StorageType<ST>
 // Aligned 16-byte shared-memory stores of kVec post-collision values of plane i
 // (conflict-free; the tile row stride Q*W*sizeof(CT) is a multiple of 16 bytes).
 template <int Q>
-__device__ __forceinline__ void store4(float* p, const float (&g)[kVec][Q], int i) {
+__device__ __forceinline__ void store4(float* p, const float (&g)[4][Q], int i) {
   *reinterpret_cast<float4*>(p) = make_float4(g[0][i], g[1][i], g[2][i], g[3][i]);
 }
 template <int Q>
-__device__ __forceinline__ void store4(double* p, const double (&g)[kVec][Q], int i) {
+__device__ __forceinline__ void store4(double* p, const double (&g)[4][Q], int i) {
   reinterpret_cast<double2*>(p)[0] = make_double2(g[0][i], g[1][i]);
   reinterpret_cast<double2*>(p)[1] = make_double2(g[2][i], g[3][i]);
 }
 
-// Four scaled FP16 values of plane i, rounded to storage, as one aligned 8-byte store.
+// Eight scaled FP16 values of plane i, rounded to storage, as two aligned 8-byte stores
+// (the tile column kHalo + 8 t is 8-byte aligned).
 template <int Q>
-__device__ __forceinline__ void store4_half(__half* p, const float (&g)[kVec][Q], int i, float inv_scale) {
-  __half o[kVec];
+__device__ __forceinline__ void store4(__half* p, const float (&g)[8][Q], int i, float inv_scale) {
+  __half o[8];
 #pragma unroll
-  for (int u = 0; u < kVec; ++u) from_compute(g[u][i], inv_scale, &o[u]);
-  const __half2 a = __halves2half2(o[0], o[1]), b = __halves2half2(o[2], o[3]);
-  *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+  for (int u = 0; u < 8; ++u) from_compute(g[u][i], inv_scale, &o[u]);
+  uint32_t w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __half2 a = __halves2half2(o[2 * j], o[2 * j + 1]);
+    w[j] = *reinterpret_cast<const uint32_t*>(&a);
+  }
+  reinterpret_cast<uint2*>(p)[0] = make_uint2(w[0], w[1]);
+  reinterpret_cast<uint2*>(p)[1] = make_uint2(w[2], w[3]);
 }
 
 template <int Q, int ST>
-__global__ void __launch_bounds__(kStreamThreads) stream_step_kernel(Arena src, Arena dst,
+__global__ void __launch_bounds__(StreamShape<ST>::kThreads) stream_step_kernel(Arena src, Arena dst,
                                                                      const RunDesc* __restrict__ runs,
                                                                      const Tile* __restrict__ tiles) {
   using T = typename StorageType<ST>::type;
   using CT = typename StorageType<ST>::compute;
   using ET = TileType<ST>;
   constexpr bool kHalf = ST == kF16S;
+  constexpr int kVec = StreamShape<ST>::kVec;
+  constexpr int kStreamThreads = StreamShape<ST>::kThreads;
   constexpr int C = cmax_of(Q);
   constexpr int W = kTile + 2 * kHalo;
   static_assert(W % 8 == 0, "tile rows of halves must start 16-byte aligned");
@@ -111,7 +130,7 @@ __global__ void __launch_bounds__(kStreamThreads) stream_step_kernel(Arena src, 
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
           T v[kVec];
-          Vec4<T>::load(fs + (int64_t)i * src.plane + x0 + k0, v);
+          VecLoad<T>::load(fs + (int64_t)i * src.plane + x0 + k0, v);
 #pragma unroll
           for (int u = 0; u < kVec; ++u) g[u][i] = to_compute(v[u], k.scale);
         }
@@ -127,7 +146,7 @@ __global__ void __launch_bounds__(kStreamThreads) stream_step_kernel(Arena src, 
       if (k0 + kVec <= len) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-          if constexpr (kHalf) store4_half(sm + i * W + kHalo + k0, g, i, k.inv_scale);
+          if constexpr (kHalf) store4(sm + i * W + kHalo + k0, g, i, k.inv_scale);
           else store4(sm + i * W + kHalo + k0, g, i);
         }
       } else {
@@ -203,7 +222,7 @@ cudaError_t prepare_stream_t() {
 
 template <int Q, int ST>
 cudaError_t launch_stream_t(Arena src, Arena dst, const RunDesc* runs, const Tile* tiles, int ntiles, cudaStream_t s) {
-  stream_step_kernel<Q, ST><<<ntiles, kStreamThreads, stream_smem<Q, ST>(), s>>>(src, dst, runs, tiles);
+  stream_step_kernel<Q, ST><<<ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s>>>(src, dst, runs, tiles);
   return cudaGetLastError();
 }
 
