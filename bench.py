@@ -51,7 +51,7 @@ GUARD_EVERY = 500
 # plan (sites per thread, threads per block, blocks per whole-lattice work group,
 # single-block bundles merged into pairs, steps between the halo exchanges of halved
 # lattices).  A plan not listed, or a kernel changed since the capture, reports null.
-PROFILED_TRAFFIC: dict = {}
+PROFILED_TRAFFIC = {("d1q7_ensemble_4096x[256,8192]", "f32", 18, 256, 2, 1, 32): 959.645440e6}
 FLOP_PER_SITE_UPDATE = {7: 39, 5: 27}  # folded step, FMA = 2 flops: 6Q - 3
 # tau = 1 collapse: per c = 1..c_max two adds, an fma, an add, a mul, two fmas, then one add (FMA = 2)
 COLLAPSE_FLOP_PER_SITE_UPDATE = {7: 31, 5: 21}
