@@ -51,7 +51,7 @@ GUARD_EVERY = 500
 # plan (sites per thread, threads per block, blocks per whole-lattice work group,
 # single-block bundles merged into pairs, steps between the halo exchanges of halved
 # lattices).  A plan not listed, or a kernel changed since the capture, reports null.
-PROFILED_TRAFFIC = {("d1q7_ensemble_4096x[256,8192]", "f32", 18, 256, 2, 1, 32): 959.645440e6}
+PROFILED_TRAFFIC = {("d1q7_ensemble_4096x[256,8192]", "f32", 20, 256, 2, 1, 32): 957.024000e6}
 FLOP_PER_SITE_UPDATE = {7: 39, 5: 27}  # folded step, FMA = 2 flops: 6Q - 3
 # tau = 1 collapse: per c = 1..c_max two adds, an fma, an add, a mul, two fmas, then one add (FMA = 2)
 COLLAPSE_FLOP_PER_SITE_UPDATE = {7: 31, 5: 21}
@@ -426,9 +426,10 @@ def stream_long(lb, torch, stream, local, launches=200, warmup=20):
 
     wl = workloads.long_lattice()
     peaks, src = measured_peaks()
-    out = {"workload": wl.name, "sites": wl.sites, "launches_timed": launches, "kernel": "stream_step_kernel",
+    out = {"workload": wl.name, "sites": wl.sites, "launches_timed": launches,
            "peak_basis": f"hbm_gbs of MEASURED_PEAKS.json ({src})"}
-    for name, prec, elem in (("f32", lb.F32, 4), ("f16s", lb.F16S, 2)):
+    for name, prec, elem, kname in (("f32", lb.F32, 4, "stream_step_kernel<7,F32>"),
+                                    ("f16s", lb.F16S, 2, "stream_step_kernel_f16<7>")):
         o = lb.lb_ks_default_opts(precision=prec, recentre_every=0, kernel=lb.KERNEL_STREAM, stream=stream)
         h = lb.lb_ks_batch_init(wl.scheme, wl.N, wl.L, wl.dt, wl.tau, wl.rho0, o)
         try:
@@ -439,7 +440,7 @@ def stream_long(lb, torch, stream, local, launches=200, warmup=20):
             lb.lb_ks_free(h)
         launch_s = tot * 1e-3 / launches
         gbs = 2 * wl.scheme * elem * wl.sites / launch_s / 1e9
-        out[name] = {"ms_per_launch": launch_s * 1e3, "gb_per_s": gbs, "peak": peaks["hbm_gbs"],
+        out[name] = {"kernel": kname, "ms_per_launch": launch_s * 1e3, "gb_per_s": gbs, "peak": peaks["hbm_gbs"],
                      "frac": gbs / peaks["hbm_gbs"], "bytes_per_site_update": 2 * wl.scheme * elem,
                      "site_updates_per_s": wl.sites / launch_s, "gpu_launches": int(nl), "clocks": clocks,
                      "l2": f"state {wl.sites * wl.scheme * elem / 1e6:.0f} MB > 129 MB L2"}

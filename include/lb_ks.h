@@ -114,7 +114,7 @@ typedef struct lb_ks_opts {
     int32_t kernel;            /* LB_KS_KERNEL_* */
     int32_t steps_per_launch;  /* resident kernel: steps kept on chip per launch; 0 = auto.  For
                                   the tau = 1 collapse, 1 selects its streaming kernel */
-    int32_t sites_per_thread;  /* resident kernel: register slots per thread (4,6,8,12,16,18 for
+    int32_t sites_per_thread;  /* resident kernel: register slots per thread (4,6,8,12,16,18,20 for
                                   F32/F16S; 4,6,8 for F64; the tau = 1 collapse: 8,16,32 for
                                   F32, 8,16 for F64); 0 = auto */
     int32_t threads_per_block; /* resident kernel: a multiple of 32 up to 512; 0 = auto */

@@ -235,8 +235,9 @@ bool valid_opts(const lb_ks_opts& o, std::string* why) {
   if (o.kernel == LB_KS_KERNEL_COLLAPSE && o.precision == LB_KS_F16S) { *why = "the tau = 1 collapse stores F64 or F32"; return false; }
   if (o.steps_per_launch < 0) { *why = "opts.steps_per_launch must be >= 0"; return false; }
   if (o.sites_per_thread != 0 && o.sites_per_thread != 4 && o.sites_per_thread != 6 && o.sites_per_thread != 8 &&
-      o.sites_per_thread != 12 && o.sites_per_thread != 16 && o.sites_per_thread != 18 && o.sites_per_thread != 32) {
-    *why = "opts.sites_per_thread must be 0, 4, 6, 8, 12, 16, 18 or 32"; return false;
+      o.sites_per_thread != 12 && o.sites_per_thread != 16 && o.sites_per_thread != 18 && o.sites_per_thread != 20 &&
+      o.sites_per_thread != 32) {
+    *why = "opts.sites_per_thread must be 0, 4, 6, 8, 12, 16, 18, 20 or 32"; return false;
   }
   if (o.threads_per_block != 0 && (o.threads_per_block < 32 || o.threads_per_block > 512 || o.threads_per_block % 32)) {
     *why = "opts.threads_per_block must be 0 or a multiple of 32 in [32, 512]"; return false;
@@ -321,7 +322,7 @@ int setup_resident(lb_ks* h, bool required, int S_force = 0, int NT_force = 0, d
   else if (h->opts.sites_per_thread) cand.push_back(h->opts.sites_per_thread);
   else if (col) cand = h->prec == kF64 ? std::vector<int>{16, 8} : std::vector<int>{32, 16, 8};
   else if (h->prec == kF64) cand = {8, 6, 4};
-  else cand = {18, 12, 8, 16, 6, 4};
+  else cand = {20, 18, 12, 8, 16, 6, 4};
   const int R = h->opts.recentre_every;
   for (int S : cand) {
     const int NT = NT_force ? NT_force
@@ -591,7 +592,7 @@ int autotune_resident(lb_ks* h) {
   } else if (h->prec == kF64) {
     tilings = {{8, 256}, {6, 256}, {4, 256}};
   } else {
-    tilings = {{18, 256}, {12, 384}, {16, 256}, {8, 512}};
+    tilings = {{20, 256}, {18, 256}, {12, 384}, {16, 256}, {8, 512}};
   }
   for (auto& tl : tilings) {
     const int NT = tl.second ? tl.second : (col ? 256 : default_threads(h->prec, tl.first));

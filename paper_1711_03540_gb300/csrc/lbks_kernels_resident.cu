@@ -30,7 +30,7 @@ cudaError_t launch_t(const ResidentLaunch& L, cudaStream_t s) {
 bool resident_supported(int Q, int storage, int S, int NT) {
   if (Q != 5 && Q != 7) return false;
   if (storage != kF64 && storage != kF32 && storage != kF16S) return false;
-  if (S != 4 && S != 6 && S != 8 && S != 12 && S != 16 && S != 18) return false;
+  if (S != 4 && S != 6 && S != 8 && S != 12 && S != 16 && S != 18 && S != 20) return false;
   if (storage == kF64 && S > 8) return false;
   const int maxt = storage == kF64 ? 256 : (S <= 8 ? 512 : (S <= 12 ? 384 : 256));
   return NT >= 32 && NT <= maxt && NT % 32 == 0;

@@ -91,13 +91,9 @@ __device__ __forceinline__ void store4(__half* p, const float (&g)[8][Q], int i,
   reinterpret_cast<uint2*>(p)[1] = make_uint2(w[2], w[3]);
 }
 
-// Scaled FP16: at most 64 registers, so that 8 blocks (32 warps) share an SM: the kernel
-// is bound by load latency, and the occupancy outweighs the few spilled values
-// (5.61 -> 5.93 TB/s on the 2^24-site lattice).
 template <int Q, int ST>
-__global__ void __launch_bounds__(StreamShape<ST>::kThreads, ST == kF16S ? 8 : 1) stream_step_kernel(Arena src, Arena dst,
-                                                                     const RunDesc* __restrict__ runs,
-                                                                     const Tile* __restrict__ tiles) {
+__device__ __forceinline__ void stream_step(Arena src, Arena dst, const RunDesc* __restrict__ runs,
+                                            const Tile* __restrict__ tiles) {
   using T = typename StorageType<ST>::type;
   using CT = typename StorageType<ST>::compute;
   using ET = TileType<ST>;
@@ -213,19 +209,45 @@ __global__ void __launch_bounds__(StreamShape<ST>::kThreads, ST == kF16S ? 8 : 1
 }
 
 template <int Q, int ST>
+__global__ void __launch_bounds__(StreamShape<ST>::kThreads) stream_step_kernel(Arena src, Arena dst,
+                                                                                 const RunDesc* __restrict__ runs,
+                                                                                 const Tile* __restrict__ tiles) {
+  stream_step<Q, ST>(src, dst, runs, tiles);
+}
+
+// Scaled FP16: registers for 8 blocks (32 warps) per SM.  The kernel is bound by load
+// latency; at 64 registers a few values spill, and the occupancy outweighs them (5.61 ->
+// 5.93 TB/s on the 2^24-site lattice).  (An explicit minimum for FP32 and FP64 changes
+// the compiler's choice even where it does not bind: FP32 took 80 registers instead of
+// 48 with a minimum of one block and ran 8 % slower.)
+template <int Q>
+__global__ void __launch_bounds__(StreamShape<kF16S>::kThreads, 8) stream_step_kernel_f16(Arena src, Arena dst,
+                                                                                       const RunDesc* __restrict__ runs,
+                                                                                       const Tile* __restrict__ tiles) {
+  stream_step<Q, kF16S>(src, dst, runs, tiles);
+}
+
+template <int Q, int ST>
 size_t stream_smem() {
   return sizeof(TileType<ST>) * Q * (kTile + 2 * kHalo);
 }
 
 template <int Q, int ST>
 cudaError_t prepare_stream_t() {
-  return cudaFuncSetAttribute(stream_step_kernel<Q, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)stream_smem<Q, ST>());
+  if constexpr (ST == kF16S)
+    return cudaFuncSetAttribute(stream_step_kernel_f16<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stream_smem<Q, ST>());
+  else
+    return cudaFuncSetAttribute(stream_step_kernel<Q, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stream_smem<Q, ST>());
 }
 
 template <int Q, int ST>
 cudaError_t launch_stream_t(Arena src, Arena dst, const RunDesc* runs, const Tile* tiles, int ntiles, cudaStream_t s) {
-  stream_step_kernel<Q, ST><<<ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s>>>(src, dst, runs, tiles);
+  if constexpr (ST == kF16S)
+    stream_step_kernel_f16<Q><<<ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s>>>(src, dst, runs, tiles);
+  else
+    stream_step_kernel<Q, ST><<<ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s>>>(src, dst, runs, tiles);
   return cudaGetLastError();
 }
 

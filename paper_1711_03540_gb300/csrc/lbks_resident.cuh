@@ -717,6 +717,7 @@ size_t smem_bytes_t(int NT) {
       case 12: if constexpr (STc != kF64) { constexpr int Sc = 12; OP; } break;       \
       case 16: if constexpr (STc != kF64) { constexpr int Sc = 16; OP; } break;       \
       case 18: if constexpr (STc != kF64) { constexpr int Sc = 18; OP; } break;       \
+      case 20: if constexpr (STc != kF64) { constexpr int Sc = 20; OP; } break;       \
       default: break;                                                                 \
     }                                                                                 \
   }
