@@ -129,98 +129,113 @@ __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e
   e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
 }
 
-// FP64 rho and rho^2 sums of the sites k0, k0 + stride, ... < len of one tile.
-// FP64 storage: plain FP64 arithmetic.  FP32/FP16 storage: the per-site sum and the
-// per-thread accumulators are kept as unevaluated pairs of floats (TwoSum), which
-// carries ~48 bits through GB300's wide FP32 pipe instead of its narrow FP64 pipe;
-// the pairs are converted to FP64 once per thread.
+// An unevaluated sum h + l of two floats (|l| <= ulp(h) / 2 after renormalisation):
+// ~48 bits carried on GB300's wide FP32 pipe instead of its narrow FP64 pipe.
+struct F2 {
+  float h, l;
+};
+
+// (a.h + a.l) + (b.h + b.l): the high parts added error-free, the error and the low
+// parts added to it, the result renormalised (both steps TwoSum).
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  F2 r;
+  two_sum(s, e, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ F2 f2_shfl_xor(F2 a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+
+// One site of FP32/FP16 storage into the thread's sums: rho = rhobar + sum_i g_i as a
+// pair (TwoSum per plane, then renormalised), then m += rho and e += rho^2 (the low part
+// of hi^2 exact by FMA, 2 hi lo added to it).
+template <int Q>
+__device__ __forceinline__ void site_pair(const float (&g)[Q], const F2 rb, F2& m, F2& e) {
+  float hi = rb.h, lo = rb.l, t, te;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    two_sum(hi, g[i], t, te);
+    hi = t;
+    lo = __fadd_rn(lo, te);
+  }
+  two_sum(hi, lo, hi, lo);  // renormalise
+  two_sum(m.h, hi, t, te);
+  m.h = t;
+  m.l = __fadd_rn(m.l, __fadd_rn(te, lo));
+  const float p = __fmul_rn(hi, hi);
+  const float pe = __fmaf_rn(hi, hi, -p);  // exact low part of hi^2
+  two_sum(e.h, p, t, te);
+  e.h = t;
+  e.l = __fadd_rn(e.l, __fadd_rn(te, __fmaf_rn(2.f * hi, lo, pe)));
+}
+
+// FP64 storage: FP64 rho and rho^2 sums of the sites k0, k0 + stride, ... < len of one tile.
+template <int Q>
+__device__ __forceinline__ void site_sums_f64(const double* f, int64_t plane, const RunDesc& d, int k0, int len,
+                                              int stride, double& m, double& e) {
+  m = 0.0;
+  e = 0.0;
+  for (int k = k0; k < len; k += stride) {
+    double rho = d.rhobar;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += f[(int64_t)i * plane + k];
+    m += rho;
+    e = __fma_rn(rho, rho, e);
+  }
+}
+
+// FP32/FP16 storage: the same sums as pairs (site_pair), sites k0, k0 + stride, ...
 template <int Q, int ST>
-__device__ __forceinline__ void site_sums(const typename StorageType<ST>::type* f, int64_t plane, const RunDesc& d,
-                                          int k0, int len, int stride, double& m, double& e) {
-  using CT = typename StorageType<ST>::compute;
-  if constexpr (ST == kF64) {
-    m = 0.0;
-    e = 0.0;
-    for (int k = k0; k < len; k += stride) {
-      double rho = d.rhobar;
+__device__ __forceinline__ void site_sums_pair(const typename StorageType<ST>::type* f, int64_t plane,
+                                               const RunDesc& d, const F2 rb, int k0, int len, int stride, F2& m,
+                                               F2& e) {
+  m = {0.f, 0.f};
+  e = {0.f, 0.f};
+  for (int k = k0; k < len; k += stride) {
+    float g[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) rho += f[(int64_t)i * plane + k];
-      m += rho;
-      e = __fma_rn(rho, rho, e);
-    }
-  } else {
-    const float rb_hi = (float)d.rhobar, rb_lo = (float)(d.rhobar - (double)rb_hi);
-    float mh = 0.f, ml = 0.f, eh = 0.f, el = 0.f;
-    for (int k = k0; k < len; k += stride) {
-      float hi = rb_hi, lo = rb_lo, t, te;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        two_sum(hi, to_compute(f[(int64_t)i * plane + k], static_cast<CT>(d.scale)), t, te);
-        hi = t;
-        lo = __fadd_rn(lo, te);
-      }
-      two_sum(hi, lo, hi, lo);  // renormalise
-      two_sum(mh, hi, t, te);
-      mh = t;
-      ml = __fadd_rn(ml, __fadd_rn(te, lo));
-      const float p = __fmul_rn(hi, hi);
-      const float pe = __fmaf_rn(hi, hi, -p);  // exact low part of hi^2
-      two_sum(eh, p, t, te);
-      eh = t;
-      el = __fadd_rn(el, __fadd_rn(te, __fmaf_rn(2.f * hi, lo, pe)));
-    }
-    m = (double)mh + (double)ml;
-    e = (double)eh + (double)el;
+    for (int i = 0; i < Q; ++i) g[i] = to_compute(f[(int64_t)i * plane + k], d.scalef);
+    site_pair<Q>(g, rb, m, e);
   }
 }
 
 // FP32 storage, tile start 16-byte aligned: thread k sums sites 4k .. 4k+3 of the tile,
-// one 16-byte load per plane (the per-site arithmetic of site_sums, sites in order).
+// one 16-byte load per plane (site_pair per site, sites in order).
 template <int Q>
-__device__ __forceinline__ void site_sums_vec4(const float* f, int64_t plane, const RunDesc& d, int k, int len,
-                                               double& m, double& e) {
-  const float rb_hi = (float)d.rhobar, rb_lo = (float)(d.rhobar - (double)rb_hi);
-  float mh = 0.f, ml = 0.f, eh = 0.f, el = 0.f;
+__device__ __forceinline__ void site_sums_vec4(const float* f, int64_t plane, const F2 rb, int k, int len, F2& m,
+                                               F2& e) {
+  m = {0.f, 0.f};
+  e = {0.f, 0.f};
   const int x = 4 * k;
-  if (x < len) {
-    float v[Q][4];
+  if (x >= len) return;
+  float v[4][Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const float* p = f + (int64_t)i * plane + x;
-      if (x + 4 <= len) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        v[i][0] = q.x; v[i][1] = q.y; v[i][2] = q.z; v[i][3] = q.w;
-      } else {
+  for (int i = 0; i < Q; ++i) {
+    const float* p = f + (int64_t)i * plane + x;
+    if (x + 4 <= len) {
+      const float4 q = *reinterpret_cast<const float4*>(p);
+      v[0][i] = q.x; v[1][i] = q.y; v[2][i] = q.z; v[3][i] = q.w;
+    } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[i][u] = x + u < len ? p[u] : 0.f;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (x + u >= len) break;
-      float hi = rb_hi, lo = rb_lo, t, te;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        two_sum(hi, v[i][u], t, te);
-        hi = t;
-        lo = __fadd_rn(lo, te);
-      }
-      two_sum(hi, lo, hi, lo);  // renormalise
-      two_sum(mh, hi, t, te);
-      mh = t;
-      ml = __fadd_rn(ml, __fadd_rn(te, lo));
-      const float p2 = __fmul_rn(hi, hi);
-      const float pe = __fmaf_rn(hi, hi, -p2);  // exact low part of hi^2
-      two_sum(eh, p2, t, te);
-      eh = t;
-      el = __fadd_rn(el, __fadd_rn(te, __fmaf_rn(2.f * hi, lo, pe)));
+      for (int u = 0; u < 4; ++u) v[u][i] = x + u < len ? p[u] : 0.f;
     }
   }
-  m = (double)mh + (double)ml;
-  e = (double)eh + (double)el;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (x + u >= len) break;
+    site_pair<Q>(v[u], rb, m, e);
+  }
 }
 
-// Guard, pass 1: FP64 sums of rho and rho^2 over one tile (fixed-order tree).
+// Guard, pass 1: sums of rho and rho^2 over one tile (fixed-order tree), stored as FP64.
+// FP64 storage sums in FP64.  FP32/FP16 storage keeps the sums as float pairs through
+// the warp tree and the warps' sum (thread 0), converted to FP64 once per tile: the
+// narrow FP64 pipe (about 1/40 of the FP32 rate on this part) would otherwise
+// take most of the pass.
 template <int Q, int ST>
 __global__ void __launch_bounds__(kPlainThreads) mass_partials_kernel(Arena src, const RunDesc* __restrict__ runs,
                                                                       const Tile* __restrict__ tiles,
@@ -228,26 +243,54 @@ __global__ void __launch_bounds__(kPlainThreads) mass_partials_kernel(Arena src,
   using T = typename StorageType<ST>::type;
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
-  double m, e;
   const T* const base = static_cast<const T*>(src.f) + d.off + tl.x0;
-  if (ST == kF32 && Q > 1 && ((d.off + tl.x0) & 3) == 0 && (src.plane & 3) == 0 && tl.len <= 4 * (int)blockDim.x)
-    site_sums_vec4<Q>(reinterpret_cast<const float*>(base), src.plane, d, threadIdx.x, tl.len, m, e);
-  else
-    site_sums<Q, ST>(base, src.plane, d, threadIdx.x, tl.len, blockDim.x, m, e);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    m += __shfl_xor_sync(0xffffffffu, m, o);
-    e += __shfl_xor_sync(0xffffffffu, e, o);
-  }
-  __shared__ double sm[2][kPlainThreads / 32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { sm[0][w] = m; sm[1][w] = e; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mm = 0.0, ee = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { mm += sm[0][i]; ee += sm[1][i]; }
-    partials[2 * blockIdx.x] = mm;
-    partials[2 * blockIdx.x + 1] = ee;
+  if constexpr (ST == kF64) {
+    double m, e;
+    site_sums_f64<Q>(base, src.plane, d, threadIdx.x, tl.len, blockDim.x, m, e);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m += __shfl_xor_sync(0xffffffffu, m, o);
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    __shared__ double sm[2][kPlainThreads / 32];
+    if (lane == 0) { sm[0][w] = m; sm[1][w] = e; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double mm = 0.0, ee = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { mm += sm[0][i]; ee += sm[1][i]; }
+      partials[2 * blockIdx.x] = mm;
+      partials[2 * blockIdx.x + 1] = ee;
+    }
+  } else {
+    // rhobar as a float pair, formed once per tile
+    __shared__ float s_rb[2];
+    if (threadIdx.x == 0) {
+      const float hi = (float)d.rhobar;
+      s_rb[0] = hi;
+      s_rb[1] = (float)(d.rhobar - (double)hi);
+    }
+    __syncthreads();
+    const F2 rb{s_rb[0], s_rb[1]};
+    F2 m, e;
+    if (ST == kF32 && Q > 1 && ((d.off + tl.x0) & 3) == 0 && (src.plane & 3) == 0 && tl.len <= 4 * (int)blockDim.x)
+      site_sums_vec4<Q>(reinterpret_cast<const float*>(base), src.plane, rb, threadIdx.x, tl.len, m, e);
+    else
+      site_sums_pair<Q, ST>(base, src.plane, d, rb, threadIdx.x, tl.len, blockDim.x, m, e);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m = f2_add(m, f2_shfl_xor(m, o));
+      e = f2_add(e, f2_shfl_xor(e, o));
+    }
+    __shared__ F2 sm[2][kPlainThreads / 32];
+    if (lane == 0) { sm[0][w] = m; sm[1][w] = e; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      F2 mm = sm[0][0], ee = sm[1][0];
+      for (int i = 1; i < (int)(blockDim.x >> 5); ++i) { mm = f2_add(mm, sm[0][i]); ee = f2_add(ee, sm[1][i]); }
+      partials[2 * blockIdx.x] = (double)mm.h + (double)mm.l;
+      partials[2 * blockIdx.x + 1] = (double)ee.h + (double)ee.l;
+    }
   }
 }
 
