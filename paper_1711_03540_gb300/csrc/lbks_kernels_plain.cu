@@ -8,8 +8,63 @@ namespace {
 
 constexpr int kPlainThreads = 256;
 
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum, six rounded operations).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// An unevaluated sum h + l of two floats (|l| <= ulp(h) / 2 after renormalisation):
+// ~48 bits carried on GB300's wide FP32 pipe instead of its narrow FP64 pipe.
+struct F2 {
+  float h, l;
+};
+
+// (a.h + a.l) + (b.h + b.l): the high parts added error-free, the error and the low
+// parts added to it, the result renormalised (both steps TwoSum).
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  F2 r;
+  two_sum(s, e, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ F2 f2_shfl_xor(F2 a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+
+// x as a pair: its float rounding and the float rounding of the rest (exact to ~48 bits).
+__device__ __forceinline__ F2 f2_of(double x) {
+  const float h = (float)x;
+  return {h, (float)__dsub_rn(x, (double)h)};
+}
+
+// a b as a pair: the high product's rounding error exact by FMA, the cross terms
+// added to it, then renormalised (|error| << |product|, so Fast2Sum suffices).
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float h = __fadd_rn(p, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+
 // f_i = f^eq_i(rho0) = A_i rho0 + B_i rho0^2 (Sec. 2, Eq. feq and its D1Q7 form),
-// evaluated in FP64 and stored as the deviation g_i = f_i - w0_i rhobar.
+// stored as the deviation g_i = f_i - w0_i rhobar.  FP64 storage: evaluated in FP64.
+// FP32/FP16 storage: evaluated in float pairs (f2_mul, f2_add: ~48 bits, more than
+// the stored float keeps) and rounded once to the compute float; the coefficients'
+// pairs are formed once per tile.  GB300's FP64 pipe would otherwise bound the pass
+// (about 20 FP64 operations per site).
 template <int Q, int ST>
 __global__ void __launch_bounds__(kPlainThreads) init_eq_kernel(Arena dst, const RunDesc* __restrict__ runs,
                                                                 const Tile* __restrict__ tiles,
@@ -19,20 +74,43 @@ __global__ void __launch_bounds__(kPlainThreads) init_eq_kernel(Arena dst, const
   using CT = typename StorageType<ST>::compute;
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
-  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-    const int64_t x = tl.x0 + k;
-    const double rho = rho0[rho_off[tl.run] + x];
-    T* f = static_cast<T*>(dst.f) + d.off + x;
+  if constexpr (ST == kF64) {
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+      const int64_t x = tl.x0 + k;
+      const double rho = rho0[rho_off[tl.run] + x];
+      T* f = static_cast<T*>(dst.f) + d.off + x;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      double v = __fma_rn(d.B[i], __dmul_rn(rho, rho), __dmul_rn(d.A[i], rho));
-      if (i == 0) v = __dsub_rn(v, d.rhobar);
-      from_compute(static_cast<CT>(v), static_cast<CT>(d.inv_scale), f + (int64_t)i * dst.plane);
+      for (int i = 0; i < Q; ++i) {
+        double v = __fma_rn(d.B[i], __dmul_rn(rho, rho), __dmul_rn(d.A[i], rho));
+        if (i == 0) v = __dsub_rn(v, d.rhobar);
+        from_compute(static_cast<CT>(v), static_cast<CT>(d.inv_scale), f + (int64_t)i * dst.plane);
+      }
+    }
+  } else {
+    __shared__ F2 s_c[2 * Q + 1];  // A_i, B_i, -rhobar
+    if ((int)threadIdx.x < 2 * Q + 1) {
+      const int c = threadIdx.x;
+      s_c[c] = f2_of(c < Q ? d.A[c] : (c < 2 * Q ? d.B[c - Q] : -d.rhobar));
+    }
+    __syncthreads();
+    const float inv = d.inv_scalef;
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+      const int64_t x = tl.x0 + k;
+      const F2 r = f2_of(rho0[rho_off[tl.run] + x]);
+      const F2 r2 = f2_mul(r, r);
+      T* f = static_cast<T*>(dst.f) + d.off + x;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        F2 v = f2_add(f2_mul(s_c[Q + i], r2), f2_mul(s_c[i], r));
+        if (i == 0) v = f2_add(v, s_c[2 * Q]);
+        from_compute(__fadd_rn(v.h, v.l), inv, f + (int64_t)i * dst.plane);
+      }
     }
   }
 }
 
-// rho = rhobar + sum_i g_i, accumulated in FP64.
+// rho = rhobar + sum_i g_i.  FP64 storage: accumulated in FP64.  FP32/FP16 storage: as
+// a float pair (TwoSum per plane), converted to FP64 exactly once per site.
 template <int Q, int ST>
 __global__ void __launch_bounds__(kPlainThreads) gather_rho_kernel(Arena src, const RunDesc* __restrict__ runs,
                                                                    const Tile* __restrict__ tiles,
@@ -42,13 +120,33 @@ __global__ void __launch_bounds__(kPlainThreads) gather_rho_kernel(Arena src, co
   using CT = typename StorageType<ST>::compute;
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
-  for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
-    const int64_t x = tl.x0 + k;
-    const T* f = static_cast<const T*>(src.f) + d.off + x;
-    double rho = d.rhobar;
+  if constexpr (ST == kF64) {
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+      const int64_t x = tl.x0 + k;
+      const T* f = static_cast<const T*>(src.f) + d.off + x;
+      double rho = d.rhobar;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) rho += static_cast<double>(to_compute(f[(int64_t)i * src.plane], static_cast<CT>(d.scale)));
-    out[out_off[tl.run] + x] = rho;
+      for (int i = 0; i < Q; ++i) rho += static_cast<double>(to_compute(f[(int64_t)i * src.plane], static_cast<CT>(d.scale)));
+      out[out_off[tl.run] + x] = rho;
+    }
+  } else {
+    __shared__ F2 s_rb;
+    if (threadIdx.x == 0) s_rb = f2_of(d.rhobar);
+    __syncthreads();
+    const F2 rb = s_rb;
+    const float scale = d.scalef;
+    for (int k = threadIdx.x; k < tl.len; k += blockDim.x) {
+      const int64_t x = tl.x0 + k;
+      const T* f = static_cast<const T*>(src.f) + d.off + x;
+      float hi = rb.h, lo = rb.l, t, te;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        two_sum(hi, to_compute(f[(int64_t)i * src.plane], scale), t, te);
+        hi = t;
+        lo = __fadd_rn(lo, te);
+      }
+      out[out_off[tl.run] + x] = (double)hi + (double)lo;
+    }
   }
 }
 
@@ -115,39 +213,6 @@ __global__ void __launch_bounds__(kPlainThreads) reservoir_step_kernel(Arena src
     const int64_t y = j + speed(i);
     if (y > 0 && y < d.N - 1) from_compute(g[i], k.inv_scale, fd + (int64_t)i * dst.plane + y);
   }
-}
-
-// Error-free sum: s + e == a + b exactly (Knuth's TwoSum, six rounded operations).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
-  s = __dadd_rn(a, b);
-  const double bb = __dsub_rn(s, a);
-  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
-}
-
-// An unevaluated sum h + l of two floats (|l| <= ulp(h) / 2 after renormalisation):
-// ~48 bits carried on GB300's wide FP32 pipe instead of its narrow FP64 pipe.
-struct F2 {
-  float h, l;
-};
-
-// (a.h + a.l) + (b.h + b.l): the high parts added error-free, the error and the low
-// parts added to it, the result renormalised (both steps TwoSum).
-__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
-  float s, e;
-  two_sum(a.h, b.h, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-  F2 r;
-  two_sum(s, e, r.h, r.l);
-  return r;
-}
-
-__device__ __forceinline__ F2 f2_shfl_xor(F2 a, int o) {
-  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
 }
 
 // One site of FP32/FP16 storage into the thread's sums: rho = rhobar + sum_i g_i as a
