@@ -761,17 +761,45 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
   h->N.assign(N, N + nruns);
   h->total_sites = total;
 
+  // rho0 goes up first, on the capture stream (idle until the first graph capture), so
+  // that the copy runs while the host computes the run table and plans below; the
+  // populations' clearing and rho0's statistics follow it there.  The handle's stream
+  // waits for them (stats.ev) before its first kernel that uses the populations or the
+  // run table, so that the stream synchronisations of planning's allocations do not.
+  // create() waits for the copy before it returns, so the caller's buffer is free again
+  // when it does.
+  int rc;
+  struct CopyWait {
+    cudaEvent_t ev = nullptr;
+    ~CopyWait() {
+      if (ev) {
+        cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+      }
+    }
+  } staged;
+  if ((rc = dalloc(h, &h->d_stage, (size_t)total))) return bail(rc);
+  if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "create capture stream"));
+  cudaStream_t const is = h->cap_stream;
+  if ((ce = cudaMemcpyAsync(h->d_stage, rho0, sizeof(double) * (size_t)total, cudaMemcpyDefault, is)) !=
+          cudaSuccess ||
+      (ce = cudaEventCreateWithFlags(&staged.ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (ce = cudaEventRecord(staged.ev, is)) != cudaSuccess)
+    return bail(cuda_fail(h, ce, "upload rho0"));
+
   // Per run on the host: the coefficients and the arena layout.  The statistics of rho0
-  // (finiteness, mass M0, mean rhobar, FP16 scale) are computed on the device after the
-  // upload below, while the host plans.
+  // (finiteness, mass M0, mean rhobar, FP16 scale) are computed on the device after its
+  // upload above, while the host plans.
   h->rho_off.resize(nruns + 1);
   h->rho_off[0] = 0;
   for (int32_t r = 0; r < nruns; ++r) h->rho_off[r + 1] = h->rho_off[r] + N[r];
-  h->runs_h.resize(nruns);
+  h->runs_h.clear();
+  h->runs_h.reserve(nruns);  // each descriptor written once, below
   h->mass0_h.assign(nruns, 0.0);
   int64_t off = 0;
   for (int32_t r = 0; r < nruns; ++r) {
-    RunDesc& d = h->runs_h[r];
+    RunDesc d;
     std::memset(&d, 0, sizeof(d));
     double A[7], B[7];
     // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
@@ -799,6 +827,7 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
     const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
     d.off = off + ghost;
     off += align_up(N[r] + 2 * ghost, kAlign);
+    h->runs_h.push_back(d);
   }
   h->plane = std::max<int64_t>(off, kAlign);
 
@@ -831,19 +860,16 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
     return LB_KS_OK;
   };
 
-  int rc;
   const size_t fbytes = storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane;
   for (int b = 0; b < 2; ++b) {
     unsigned char* p = nullptr;
     if ((rc = dalloc(h, &p, fbytes))) return bail(rc);
     h->fbuf[b] = p;
-    if ((ce = cudaMemset(p, 0, fbytes)) != cudaSuccess) return bail(cuda_fail(h, ce, "clear populations"));
   }
   if ((rc = dalloc(h, &h->d_runs, nruns))) return bail(rc);
   if ((rc = dalloc(h, &h->d_stream_tiles, st.size()))) return bail(rc);
   if ((rc = dalloc(h, &h->d_stream_tile_begin, st_begin.size()))) return bail(rc);
   if ((rc = dalloc(h, &h->d_rho_off, h->rho_off.size()))) return bail(rc);
-  if ((rc = dalloc(h, &h->d_stage, (size_t)total))) return bail(rc);
   if ((rc = dalloc(h, &h->d_partials, 2 * st.size()))) return bail(rc);
   if ((rc = dalloc(h, &h->d_mass0, nruns))) return bail(rc);
   if ((rc = dalloc(h, &h->d_mass, nruns))) return bail(rc);
@@ -858,34 +884,26 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
       (ce = up(h->d_rho_off, h->rho_off.data(), sizeof(int64_t) * h->rho_off.size())) != cudaSuccess ||
       (ce = cudaMemset(h->d_flags, 0, sizeof(int))) != cudaSuccess)
     return bail(cuda_fail(h, ce, "upload"));
-  // rho0 goes up on the handle's stream while the host plans below; the init kernels
-  // follow it in stream order, and create() waits for the copy (not for them) before
-  // it returns, so the caller's buffer is free again when it does.
-  struct CopyWait {
-    cudaEvent_t ev = nullptr;
-    ~CopyWait() {
-      if (ev) {
-        cudaEventSynchronize(ev);
-        cudaEventDestroy(ev);
-      }
-    }
-  } staged;
-  if ((ce = cudaMemcpyAsync(h->d_stage, rho0, sizeof(double) * (size_t)total, cudaMemcpyDefault, h->stream)) !=
-          cudaSuccess ||
-      (ce = cudaEventCreateWithFlags(&staged.ev, cudaEventDisableTiming)) != cudaSuccess ||
-      (ce = cudaEventRecord(staged.ev, h->stream)) != cudaSuccess)
-    return bail(cuda_fail(h, ce, "upload rho0"));
+  for (int b = 0; b < 2; ++b)
+    if ((ce = cudaMemsetAsync(h->fbuf[b], 0, fbytes, is)) != cudaSuccess)
+      return bail(cuda_fail(h, ce, "clear populations"));
   // rho0's statistics on the device, read back after planning (once the event after
-  // them has completed: the read-back copies are not in the handle's stream)
+  // them has completed)
   CopyWait stats;
   const int no_bad = nruns;
-  if ((ce = cudaMemcpyAsync(h->d_bad_run, &no_bad, sizeof(int), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+  if ((ce = cudaMemcpyAsync(h->d_bad_run, &no_bad, sizeof(int), cudaMemcpyHostToDevice, is)) != cudaSuccess ||
       (ce = launch_init_stats(scheme, h->prec, nruns, h->d_stage, h->d_rho_off, h->d_runs, h->d_stream_tiles,
                               h->n_stream_tiles, h->d_stream_tile_begin, h->d_partials, h->d_mass0, h->d_bad_run,
-                              h->stream)) != cudaSuccess ||
+                              is)) != cudaSuccess ||
       (ce = cudaEventCreateWithFlags(&stats.ev, cudaEventDisableTiming)) != cudaSuccess ||
-      (ce = cudaEventRecord(stats.ev, h->stream)) != cudaSuccess)
+      (ce = cudaEventRecord(stats.ev, is)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "rho0 statistics"));
+  bool init_joined = false;
+  auto join_init = [&]() -> cudaError_t {  // the handle's stream after the capture stream's init work
+    if (init_joined) return cudaSuccess;
+    init_joined = true;
+    return cudaStreamWaitEvent(h->stream, stats.ev, 0);
+  };
 
   // Kernel family.
   int kern = o.kernel;
@@ -909,8 +927,6 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
   h->kernel = kern;
   if (kern == LB_KS_KERNEL_STREAM && (ce = stream_prepare(scheme, h->prec)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "stream kernel setup"));
-  if ((ce = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-    return bail(cuda_fail(h, ce, "create capture stream"));
   // streams and events for concurrent lanes, when the plan has several (or the tuner
   // may choose one that does)
   if ((kern == LB_KS_KERNEL_RESIDENT || h->collapse_resident) && (o.autotune || h->nlanes > 1)) {
@@ -919,12 +935,14 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
         ce = cudaEventCreateWithFlags(&h->ev_join[l], cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "create lane stream"));
+    if (o.autotune && (ce = join_init()) != cudaSuccess) return bail(cuda_fail(h, ce, "join init"));
     if (o.autotune && (rc = autotune_resident(h)) != LB_KS_OK) return bail(rc);
   }
   if (h->nlanes > 1 && !h->ev_fork) return bail(fail(h, LB_KS_ECUDA, "internal: lanes without their streams"));
 
   if ((kern == LB_KS_KERNEL_COLLAPSE || kern == LB_KS_KERNEL_PLAIN || reservoir) && (rc = plain_tiles()) != LB_KS_OK)
     return bail(rc);
+  if ((ce = join_init()) != cudaSuccess) return bail(cuda_fail(h, ce, "join init"));
   if (kern == LB_KS_KERNEL_COLLAPSE) {
     // rho - rhobar in both arenas (reservoir ends and ghosts keep their values in both)
     for (int b = 0; b < 2; ++b)
@@ -1241,6 +1259,7 @@ void lb_ks_free(lb_ks_t* h) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   for (cudaStream_t ss : h->side_stream)
     if (ss) cudaStreamSynchronize(ss);
+  if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);  // init work, when create() bails out
   for (void* p : h->allocations) cudaFreeAsync(p, h->stream);  // back to the pool, in stream order
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int l = 0; l < 2; ++l) {

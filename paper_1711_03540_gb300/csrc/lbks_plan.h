@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <initializer_list>
 #include <utility>
 #include <vector>
 
@@ -40,6 +41,7 @@ inline bool plan_pieces(const std::vector<int64_t>& Ns, int C, int S, int NT, in
                         std::vector<Piece>* rings, std::vector<Piece>* segs) {
   rings->clear();
   segs->clear();
+  rings->reserve(Ns.size() + Ns.size() / 2);
   for (int32_t r = 0; r < (int32_t)Ns.size(); ++r) {
     const int64_t N = Ns[r];
     // Ring: hold m copies of the lattice around one ring of m N sites (m > 1 only
@@ -92,12 +94,28 @@ inline bool plan_pieces(const std::vector<int64_t>& Ns, int C, int S, int NT, in
   return true;
 }
 
+// Indices 0..n-1 in decreasing order of k (k >= 0), equal keys in index order: the
+// order of a stable sort, by counting (keys are thread counts, at most a few thousand).
+inline std::vector<int> stable_desc(const std::vector<int>& k) {
+  int kmax = 0;
+  for (int v : k) kmax = std::max(kmax, v);
+  std::vector<int> start((size_t)kmax + 2, 0);  // start[kmax - v]: first slot of key v
+  for (int v : k) ++start[(size_t)(kmax - v) + 1];
+  for (size_t q = 1; q < start.size(); ++q) start[q] += start[q - 1];
+  std::vector<int> idx(k.size());
+  for (size_t i = 0; i < k.size(); ++i) idx[(size_t)start[(size_t)(kmax - k[i])]++] = (int)i;
+  return idx;
+}
+
 // Work groups of one lane during packing: first fit of pieces (threads nthr) into
 // groups of `cap` threads.
 struct Bins {
   int cap = 0;
   bool pair = false;  // pair work groups: block 0 is threads [0, cap/2), block 1 the rest
-  std::vector<std::vector<int>> members;
+  // Members of each group in the order they joined it: a singly linked list over piece
+  // indices (head, tail per group; nxt per piece), so that packing allocates nothing
+  // per group.
+  std::vector<int> head, tail, count, nxt;
   std::vector<int> used;   // threads [0, used) taken (pair work groups: the end of block 1's)
   std::vector<int> used0;  // pair work groups: threads [0, used0) of block 0 taken
   std::vector<int> key;    // queue order (largest first); empty: by occupied threads
@@ -106,6 +124,30 @@ struct Bins {
   std::vector<int> tree;
   size_t tn = 0;
 
+  size_t groups() const { return used.size(); }
+  std::vector<int> members(size_t b) const {
+    std::vector<int> m;
+    for (int i = head[b]; i >= 0; i = nxt[(size_t)i]) m.push_back(i);
+    return m;
+  }
+  void link(size_t b, int i) {
+    if ((size_t)i >= nxt.size()) nxt.resize(std::max<size_t>((size_t)i + 1, 2 * nxt.size()), -1);
+    nxt[(size_t)i] = -1;
+    if (tail[b] < 0) head[b] = i;
+    else nxt[(size_t)tail[b]] = i;
+    tail[b] = i;
+    ++count[b];
+  }
+  // A new, empty group with u0 threads of block 0 (pair groups) and threads [0, u)
+  // (pair groups: block 1's up to u) taken.
+  size_t new_group(int u0, int u) {
+    head.push_back(-1);
+    tail.push_back(-1);
+    count.push_back(0);
+    used.push_back(u);
+    if (pair) used0.push_back(u0);
+    return used.size() - 1;
+  }
   int room(size_t b) const {
     int f = cap - used[b];
     if (pair) f = std::max(f, cap / 2 - used0[b]);
@@ -124,13 +166,11 @@ struct Bins {
     tree[p] = room(b);
     for (p >>= 1; p >= 1; p >>= 1) tree[p] = std::max(tree[2 * p], tree[2 * p + 1]);
   }
-  // A new group holding pieces `mem`, with u0 threads of block 0 (pair groups) and
-  // threads [0, u) (pair groups: block 1's up to u) taken.
-  void add(std::vector<int> mem, int u0, int u) {
-    members.push_back(std::move(mem));
-    used.push_back(u);
-    if (pair) used0.push_back(u0);
-    fix(used.size() - 1);
+  // A new group holding pieces `mem`, with u0 and u as for new_group.
+  void add(std::initializer_list<int> mem, int u0, int u) {
+    const size_t b = new_group(u0, u);
+    for (int i : mem) link(b, i);
+    fix(b);
   }
   // First fit: the first group with room for the piece.  A piece never spans the
   // block edge of a pair work group here: it goes into block 0's free threads or
@@ -148,7 +188,7 @@ struct Bins {
       pieces[i].t0 = used[b];
       used[b] += need;
     }
-    members[b].push_back(i);
+    link(b, i);
     fix(b);
     return true;
   }
@@ -158,24 +198,22 @@ struct Bins {
   }
   // bundles in decreasing order of occupied threads (longest first)
   void emit(const std::vector<Piece>& pieces, std::vector<Piece>* ordered, std::vector<int2>* bundles) const {
-    std::vector<int> order(members.size());
-    for (size_t b = 0; b < members.size(); ++b) order[b] = (int)b;
-    const std::vector<int>& kk = key.empty() ? used : key;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kk[a] > kk[b]; });
+    const std::vector<int> order = stable_desc(key.empty() ? used : key);
     ordered->clear();
     bundles->clear();
+    ordered->reserve(pieces.size());
+    bundles->reserve(order.size());
     for (int b : order) {
-      bundles->push_back(int2{(int)ordered->size(), (int)members[b].size()});
-      for (int i : members[b]) ordered->push_back(pieces[i]);
+      bundles->push_back(int2{(int)ordered->size(), count[(size_t)b]});
+      for (int i = head[(size_t)b]; i >= 0; i = nxt[(size_t)i]) ordered->push_back(pieces[(size_t)i]);
     }
   }
 };
 
 inline std::vector<int> by_threads_desc(const std::vector<Piece>& pieces) {
-  std::vector<int> idx(pieces.size());
-  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return pieces[a].nthr > pieces[b].nthr; });
-  return idx;
+  std::vector<int> nthr(pieces.size());
+  for (size_t i = 0; i < pieces.size(); ++i) nthr[i] = pieces[i].nthr;
+  return stable_desc(nthr);
 }
 
 // First-fit decreasing packing of whole lattices: a lattice held as two halves opens a
@@ -214,23 +252,20 @@ inline void pack_rings(std::vector<Piece>& pieces, int NT, Bins* blocks, Bins* p
 inline void merge_blocks_into_pairs(std::vector<Piece>& pieces, int NT, const Bins& blocks, Bins* pairs) {
   pairs->cap = 2 * NT;
   for (size_t b = 0; b < pairs->key.size(); ++b) pairs->key[b] += 4 * NT;
-  std::vector<int> order(blocks.members.size());
-  for (size_t b = 0; b < order.size(); ++b) order[b] = (int)b;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blocks.used[a] > blocks.used[b]; });
+  const std::vector<int> order = stable_desc(blocks.used);
   for (size_t q = 0; q < order.size(); q += 2) {
-    std::vector<int> mem = blocks.members[order[q]];
-    int used = blocks.used[order[q]];
+    const size_t a = (size_t)order[q];
+    const size_t g = pairs->new_group(blocks.used[a], q + 1 < order.size() ? NT + blocks.used[(size_t)order[q + 1]]
+                                                                           : blocks.used[a]);
+    for (int i = blocks.head[a]; i >= 0; i = blocks.nxt[(size_t)i]) pairs->link(g, i);
     if (q + 1 < order.size()) {
-      for (int i : blocks.members[order[q + 1]]) {
-        pieces[i].t0 += NT;
-        mem.push_back(i);
+      const size_t c = (size_t)order[q + 1];
+      for (int i = blocks.head[c]; i >= 0; i = blocks.nxt[(size_t)i]) {
+        pieces[(size_t)i].t0 += NT;
+        pairs->link(g, i);
       }
-      used = NT + blocks.used[order[q + 1]];
     }
-    pairs->members.push_back(mem);
-    pairs->used.push_back(used);
-    pairs->used0.push_back(blocks.used[order[q]]);
-    pairs->key.push_back(blocks.used[order[q]]);  // the fuller of the two blocks
+    pairs->key.push_back(blocks.used[a]);  // the fuller of the two blocks
   }
 }
 

@@ -7,7 +7,9 @@
 //     OK rings=<pieces> halves=<lattices> spans=<rings across a pair> segs=<pieces> blocks=<groups>
 //        pairs=<groups> segblocks=<groups> ring_threads=<threads> seg_threads=<threads>
 // or FAIL <reason>.  The line "FIRSTFIT <trials> <seed>" compares the groups' first
-// fit with a linear scan of the groups on random pieces.
+// fit with a linear scan of the groups on random pieces; "ORDER <trials> <seed>" the
+// counting sort that orders pieces and bundles with a stable sort.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <iostream>
@@ -59,10 +61,10 @@ void check_coverage(const std::vector<int64_t>& Ns, const std::vector<Piece>& al
 // piece lies in one block unless it is the one ring across both (t0 = 0, more than NT
 // threads); halves sit at thread 0 of block 0 and block 1.
 void check_groups(const Bins& g, const std::vector<Piece>& pieces, int NT, bool pair, std::vector<int>* seen) {
-  for (size_t b = 0; b < g.members.size(); ++b) {
+  for (size_t b = 0; b < g.groups(); ++b) {
     std::vector<char> used((size_t)(pair ? 2 * NT : NT), 0);
     int spans = 0, halves = 0;
-    for (int i : g.members[b]) {
+    for (int i : g.members(b)) {
       const Piece& p = pieces[(size_t)i];
       ++(*seen)[(size_t)i];
       const int lo = p.t0, hi = p.t0 + p.nthr;
@@ -108,8 +110,8 @@ std::string run_case(int C, int S, int NT, int cl, int kx, int kseg, int merge, 
 
   Bins blocks, pairs, segbins;
   pack_rings(rings, NT, &blocks, &pairs);
-  if (cl == 1) check(pairs.members.empty(), "pair groups with one-block work groups");
-  const size_t nsingle = blocks.members.size(), npair = pairs.members.size();
+  if (cl == 1) check((pairs.groups() == 0), "pair groups with one-block work groups");
+  const size_t nsingle = blocks.groups(), npair = pairs.groups();
   const bool merged = merge && npair && nsingle;
   if (merged) {
     merge_blocks_into_pairs(rings, NT, blocks, &pairs);
@@ -129,7 +131,7 @@ std::string run_case(int C, int S, int NT, int cl, int kx, int kseg, int merge, 
   size_t total = 0;
   for (const int2& b : bundles) total += (size_t)b.y;
   check(total == ordered.size(), "bundles do not cover the ordered pieces");
-  if (merged) check(pairs.members.size() == npair + (nsingle + 1) / 2, "single-block groups not two to a pair");
+  if (merged) check(pairs.groups() == npair + (nsingle + 1) / 2, "single-block groups not two to a pair");
   if (!fail_.empty()) return "FAIL " + fail_;
   int halves = 0, spans = 0;
   int64_t ring_threads = 0, seg_threads = 0;
@@ -141,7 +143,7 @@ std::string run_case(int C, int S, int NT, int cl, int kx, int kseg, int merge, 
   for (const Piece& p : segs) seg_threads += p.nthr;
   std::ostringstream o;
   o << "OK rings=" << rings.size() << " halves=" << halves / 2 << " spans=" << spans << " segs=" << segs.size()
-    << " blocks=" << blocks.members.size() << " pairs=" << pairs.members.size() << " segblocks=" << segbins.members.size()
+    << " blocks=" << blocks.groups() << " pairs=" << pairs.groups() << " segblocks=" << segbins.groups()
     << " ring_threads=" << ring_threads << " seg_threads=" << seg_threads;
   return o.str();
 }
@@ -204,6 +206,21 @@ std::string first_fit_trials(int trials, unsigned seed) {
   return "OK first fit identical to the scan in " + std::to_string(trials) + " trials";
 }
 
+// stable_desc (counting) against std::stable_sort on random keys with many ties.
+std::string order_trials(int trials, unsigned seed) {
+  std::mt19937 rng(seed);
+  for (int t = 0; t < trials; ++t) {
+    const int n = (int)(rng() % 3000), kmax = 1 + (int)(rng() % 1200);
+    std::vector<int> k(n);
+    for (int& v : k) v = (int)(rng() % (unsigned)kmax);
+    std::vector<int> ref(n);
+    for (int i = 0; i < n; ++i) ref[i] = i;
+    std::stable_sort(ref.begin(), ref.end(), [&](int a, int b) { return k[a] > k[b]; });
+    if (stable_desc(k) != ref) return "FAIL stable_desc differs from a stable sort";
+  }
+  return "OK";
+}
+
 }  // namespace
 
 int main() {
@@ -218,6 +235,13 @@ int main() {
       unsigned seed = 0;
       in >> trials >> seed;
       std::cout << first_fit_trials(trials, seed) << "\n";
+      continue;
+    }
+    if (head == "ORDER") {
+      int trials = 0;
+      unsigned seed = 0;
+      in >> trials >> seed;
+      std::cout << order_trials(trials, seed) << "\n";
       continue;
     }
     const int C = std::atoi(head.c_str());

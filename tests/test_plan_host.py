@@ -3,8 +3,9 @@ tests/plan_check.cpp against the header with g++ and checks, on the benchmark
 ensemble's lengths and on edge sets, that every site is stored by exactly one
 piece, that pieces split into runs of S and S-1 sites per thread, that halves and
 segments carry halos wide enough for the steps between exchanges, that groups hold
-disjoint thread ranges within their capacity, and that the segment-tree first fit
-chooses the same group as a linear scan.  No GPU needed."""
+disjoint thread ranges within their capacity, that the segment-tree first fit
+chooses the same group as a linear scan, and that the counting sort ordering pieces
+and bundles gives a stable sort's order.  No GPU needed."""
 import os
 import shutil
 import subprocess
@@ -98,3 +99,7 @@ def test_edge_lengths(checker):
 
 def test_first_fit_matches_linear_scan(checker):
     checker(["FIRSTFIT 200 11", "FIRSTFIT 200 12"])
+
+
+def test_counting_order_matches_stable_sort(checker):
+    checker(["ORDER 200 21", "ORDER 200 22"])
