@@ -56,6 +56,16 @@ template <> struct VecLoad<__half> {
   }
 };
 
+// Compile-time loop over I = B..E-1 (keeps every plane's speed a constant expression).
+template <int B, int E> struct StaticFor {
+  template <typename F> __device__ __forceinline__ static void run(F&& fn) {
+    if constexpr (B < E) {
+      fn(std::integral_constant<int, B>{});
+      StaticFor<B + 1, E>::run(fn);
+    }
+  }
+};
+
 // Element type of the shared-memory tile: the storage type for scaled FP16 (the
 // value is rounded to it once, where it is computed), else the compute type.
 template <int ST>
@@ -172,29 +182,48 @@ __device__ __forceinline__ void stream_step(Arena src, Arena dst, const RunDesc*
   __syncthreads();
   // Phase 2: pull f*_i(x - c_i), lane-contiguous sites, coalesced stores.
   if constexpr (kHalf) {
-    // Sites kk and kk + 1 (kk even) of plane i sit at tile columns e and e + 1,
-    // e = kHalo + kk - c_i; W and kHalo are even, so for even c_i they are one aligned
-    // 32-bit word, for odd c_i the high half of word (e - 1) / 2 and the low half of
-    // the next.  Columns read stay in [kHalo - 4, kHalo + kTile + 3] = [0, W) of the
-    // row (c_max <= 3 <= kHalo - 1); a value read past a ragged tile's end or its halo
-    // is not stored.  Rows, run offsets, the plane stride and tile starts are even, so
-    // the 4-byte global stores are aligned.
-    const uint32_t* sw = reinterpret_cast<const uint32_t*>(smem_raw);
+    // Sites kk .. kk + 7 (kk = 8 t) of plane i sit at tile columns e0 .. e0 + 7,
+    // e0 = i W + kHalo + kk - c_i, whose offset from 8 t is a compile-time constant: the
+    // eight halves come from one 16-byte, two 8-byte or four 4-byte shared loads (e0
+    // a multiple of 8, 4 or 2), or, for odd c_i, from five words, each output word the
+    // high half of one and the low half of the next; one 16-byte streaming store writes
+    // them.  Columns read stay in [kHalo - 4, kHalo + kTile + 3] = [0, W) of the row
+    // (c_max <= 3 <= kHalo - 1); values read past a ragged tile's end or its halo are
+    // not stored.  Rows, run offsets, the plane stride and tile starts are multiples of
+    // 8 halves, so the 16-byte global stores are aligned.
+    static_assert(W % 8 == 0, "tile rows of halves start 16-byte aligned");
+    const int kk = kVec * threadIdx.x;
+    if (kk < len) {
+      StaticFor<0, Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int off = i * W + kHalo - speed(i);  // e0 = off + kk
+        const unsigned char* row = smem_raw + (size_t)(off & ~1) * sizeof(__half) + (size_t)kk * sizeof(__half);
+        uint32_t w[4];
+        if constexpr (off % 8 == 0) {
+          const uint4 v = *reinterpret_cast<const uint4*>(row);
+          w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        } else if constexpr (off % 4 == 0) {
+          const uint2 a = reinterpret_cast<const uint2*>(row)[0], b = reinterpret_cast<const uint2*>(row)[1];
+          w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+        } else if constexpr (off % 2 == 0) {
 #pragma unroll
-    for (int u = 0; u < kVec / 2; ++u) {
-      const int kk = 2 * (threadIdx.x + u * kStreamThreads);
-      if (kk < len) {
+          for (int j = 0; j < 4; ++j) w[j] = reinterpret_cast<const uint32_t*>(row)[j];
+        } else {
+          uint32_t x[5];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const int e = i * W + kHalo + kk - speed(i);
-          uint32_t w;
-          if ((speed(i) & 1) == 0) w = sw[e >> 1];
-          else w = __byte_perm(sw[(e - 1) >> 1], sw[(e + 1) >> 1], 0x5432);
-          T* p = fd + (int64_t)i * dst.plane + x0 + kk;
-          if (kk + 1 < len) __stcs(reinterpret_cast<unsigned int*>(p), w);
-          else __stcs(p, __ushort_as_half((unsigned short)(w & 0xffffu)));
+          for (int j = 0; j < 5; ++j) x[j] = reinterpret_cast<const uint32_t*>(row)[j];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) w[j] = __byte_perm(x[j], x[j + 1], 0x5432);
         }
-      }
+        T* p = fd + (int64_t)i * dst.plane + x0 + kk;
+        if (kk + kVec <= len) {
+          __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < kVec; ++j)
+            if (kk + j < len) __stcs(p + j, __ushort_as_half((unsigned short)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu)));
+        }
+      });
     }
   } else {
 #pragma unroll
