@@ -149,17 +149,16 @@ def test_f16s_resident_one_step_per_launch_equals_stream(lb, Q):
 
 
 def test_f16s_stream_many_tiles_per_block_equals_resident(lb):
-    """The scaled-FP16 streaming kernel runs a persistent grid of at most SMs x 5 blocks
-    whose tiles come in through double-buffered bulk copies: with more tiles than blocks
-    (about 1100 tiles of 1024 sites: ragged tails, lattices from 7 to 2^18 sites) every
-    block walks several tiles, refilling each stage and prefetching the next tile's
-    halo.  The result equals the resident kernel at one step per launch bitwise."""
+    """Scaled FP16 at a size where the streaming kernel's tiles (1158 of 1024 sites,
+    ragged tails, lattices from 7 to 2^18 sites) outnumber the blocks the GPU holds at
+    once (SMs x 8), so that blocks of several waves write the arena: the result equals
+    the resident kernel at one step per launch bitwise."""
     rng = np.random.default_rng(44)
     Ns = np.array([1 << 18, 7, 262147, 5000, 1 << 17, 99999, 333, 2048 * 97 + 5, 1 << 16, 4097, 7, 150001],
                   dtype=np.int64)
     r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
     tiles = int(sum((n + 1023) // 1024 for n in Ns))
-    assert tiles > 152 * 5
+    assert tiles > 152 * 5  # more than the resident blocks of one wave
     args = (7, Ns, Ns * 0.1, np.full(Ns.size, 1e-4), np.linspace(1.5, 2.5, Ns.size), r0, 20)
     a, da = run_gpu(lb, *args, precision=2, kernel=2)
     b = run_gpu(lb, *args, precision=2, kernel=3, steps_per_launch=1)[0]
