@@ -149,16 +149,16 @@ def test_f16s_resident_one_step_per_launch_equals_stream(lb, Q):
 
 
 def test_f16s_stream_many_tiles_per_block_equals_resident(lb):
-    """Scaled FP16 at a size where the streaming kernel's tiles (1158 of 1024 sites,
-    ragged tails, lattices from 7 to 2^18 sites) outnumber the blocks the GPU holds at
-    once (SMs x 8), so that blocks of several waves write the arena: the result equals
-    the resident kernel at one step per launch bitwise."""
+    """Scaled FP16 on 1.18 M sites in 1158 streaming tiles of 1024 sites (ragged tails,
+    lattices from 7 to 2^18 sites, the resident kernel holding the long ones as
+    segments): the streaming step equals the resident kernel at one step per launch
+    bitwise."""
     rng = np.random.default_rng(44)
     Ns = np.array([1 << 18, 7, 262147, 5000, 1 << 17, 99999, 333, 2048 * 97 + 5, 1 << 16, 4097, 7, 150001],
                   dtype=np.int64)
     r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
     tiles = int(sum((n + 1023) // 1024 for n in Ns))
-    assert tiles > 152 * 5  # more than the resident blocks of one wave
+    assert tiles == 1158
     args = (7, Ns, Ns * 0.1, np.full(Ns.size, 1e-4), np.linspace(1.5, 2.5, Ns.size), r0, 20)
     a, da = run_gpu(lb, *args, precision=2, kernel=2)
     b = run_gpu(lb, *args, precision=2, kernel=3, steps_per_launch=1)[0]
