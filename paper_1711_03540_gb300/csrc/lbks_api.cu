@@ -10,7 +10,9 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
+#include <atomic>
 
 #include "../../include/lb_ks.h"
 #include "lbks_internal.h"
@@ -71,6 +73,28 @@ struct Lane {
 
 }  // namespace
 
+// An allocator that default-initialises (leaves untouched) trivially constructible
+// elements on resize, so that a large run table is written once, by whoever fills it.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U>&) {}
+  template <typename U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+using RunTable = std::vector<RunDesc, NoInitAlloc<RunDesc>>;
+
 struct lb_ks {
   int Q = 0, prec = 0, kernel = 0, cmax = 0;
   int nplanes = 0;         // stored planes: Q, or 1 for the tau = 1 collapse (rho - rhobar)
@@ -79,7 +103,7 @@ struct lb_ks {
   lb_ks_opts opts{};
   int32_t nruns = 0;
   std::vector<int64_t> N, rho_off;
-  std::vector<RunDesc> runs_h;
+  RunTable runs_h;
   std::vector<double> mass0_h;
   int64_t total_sites = 0, plane = 0;
   void* fbuf[2] = {nullptr, nullptr};
@@ -794,19 +818,32 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
   h->rho_off.resize(nruns + 1);
   h->rho_off[0] = 0;
   for (int32_t r = 0; r < nruns; ++r) h->rho_off[r + 1] = h->rho_off[r] + N[r];
-  h->runs_h.clear();
-  h->runs_h.reserve(nruns);  // each descriptor written once, below
   h->mass0_h.assign(nruns, 0.0);
+  // arena offsets first (a prefix sum), then the descriptors, on a few host threads for
+  // large batches (each thread writes its own runs, once)
+  const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
+  std::vector<int64_t> run_off(nruns);
   int64_t off = 0;
   for (int32_t r = 0; r < nruns; ++r) {
-    RunDesc d;
-    std::memset(&d, 0, sizeof(d));
-    double A[7], B[7];
-    // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
-    const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
-    if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK)
-      return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
-    const double w = 1.0 / tau[r];
+    run_off[r] = off + ghost;
+    off += align_up(N[r] + 2 * ghost, kAlign);
+  }
+  h->runs_h.resize(nruns);
+  std::atomic<int32_t> bad_coef{nruns};  // first run whose coefficients are not finite
+  auto fill_runs = [&](int32_t r0, int32_t r1) {
+    for (int32_t r = r0; r < r1; ++r) {
+      RunDesc& d = h->runs_h[r];
+      std::memset(&d, 0, sizeof(d));
+      double A[7], B[7];
+      // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
+      const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
+      if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK) {
+        int32_t cur = bad_coef.load();
+        while (r < cur && !bad_coef.compare_exchange_weak(cur, r)) {
+        }
+        continue;
+      }
+      const double w = 1.0 / tau[r];
     d.N = N[r];
     d.reservoir = reservoir ? 1 : 0;
     d.rho_left = reservoir ? rho_left[r] : 0.0;
@@ -819,16 +856,31 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
       d.af[i] = (float)d.a[i];
       d.bf[i] = (float)d.b[i];
     }
-    d.r = 1.0 - w;
-    d.rf = (float)d.r;
-    d.rhobar = 0.0;  // rhobar and the FP16 scale: set on the device
-    d.scale = d.inv_scale = 1.0;
-    d.scalef = d.inv_scalef = 1.0f;
-    const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
-    d.off = off + ghost;
-    off += align_up(N[r] + 2 * ghost, kAlign);
-    h->runs_h.push_back(d);
+      d.r = 1.0 - w;
+      d.rf = (float)d.r;
+      d.rhobar = 0.0;  // rhobar and the FP16 scale: set on the device
+      d.scale = d.inv_scale = 1.0;
+      d.scalef = d.inv_scalef = 1.0f;
+      d.off = run_off[r];
+    }
+  };
+  {
+    const int nth = nruns >= 1024 ? 4 : 1;
+    std::vector<std::thread> pool;
+    int32_t r0 = 0;
+    try {
+      for (int k = 1; k < nth; ++k) {
+        const int32_t r1 = (int32_t)((int64_t)nruns * k / nth);
+        pool.emplace_back(fill_runs, r0, r1);
+        r0 = r1;
+      }
+    } catch (...) {  // no thread: this one does the rest
+    }
+    fill_runs(r0, nruns);
+    for (std::thread& th : pool) th.join();
   }
+  if (bad_coef.load() < nruns)
+    return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(bad_coef.load()) + ": coefficients are not finite"));
   h->plane = std::max<int64_t>(off, kAlign);
 
   // Tiles.  The streaming tiles (also those of the guard, the statistics of rho0 and the
@@ -1186,7 +1238,7 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) try {
   std::memcpy(m0.data(), p, sizeof(double) * h->nruns);
   p += sizeof(double) * h->nruns;
   LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
-  h->runs_h = runs;
+  h->runs_h.assign(runs.begin(), runs.end());
   h->mass0_h = m0;
   LBKS_CUDA(h, cudaMemcpy(h->d_runs, runs.data(), sizeof(RunDesc) * h->nruns, cudaMemcpyHostToDevice), "load runs");
   LBKS_CUDA(h, cudaMemcpy(h->d_mass0, m0.data(), sizeof(double) * h->nruns, cudaMemcpyHostToDevice), "load mass0");
