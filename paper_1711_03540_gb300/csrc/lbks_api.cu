@@ -134,6 +134,11 @@ struct lb_ks {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t side_stream[2] = {nullptr, nullptr};  // lanes 1 and 2 of the resident kernel
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  // lb_ks_rho into pinned host memory: the streaming tiles in kRhoChunks chunks (first
+  // tile, first output site of each; the last entry ends the table), each gathered into
+  // the staging buffer and copied out while the next one is gathered
+  std::vector<std::pair<int, int64_t>> rho_chunks;
+  cudaEvent_t ev_rho = nullptr;
   int64_t steps_done = 0;
   int64_t phase = 0;  // steps since the last guard
   int64_t launches = 0;
@@ -895,6 +900,15 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
   }
   st_begin[nruns] = (int32_t)st.size();
   h->n_stream_tiles = (int)st.size();
+  {
+    constexpr int kRhoChunks = 8;
+    const int nt = (int)st.size();
+    for (int c = 0; c <= kRhoChunks; ++c) {
+      const int t = (int)((int64_t)nt * c / kRhoChunks);
+      const int64_t o0 = t < nt ? h->rho_off[st[t].run] + st[t].x0 : total;
+      if (h->rho_chunks.empty() || h->rho_chunks.back().first != t) h->rho_chunks.emplace_back(t, o0);
+    }
+  }
   auto plain_tiles = [&]() -> int {
     if (h->d_plain_tiles) return LB_KS_OK;
     std::vector<Tile> pt;
@@ -1124,19 +1138,39 @@ int lb_ks_rho(lb_ks_t* h, double* out) try {
   if (!h) return fail(nullptr, LB_KS_EINVAL, "NULL handle");
   if (h->sticky) return h->sticky;
   if (!out) return fail(h, LB_KS_EINVAL, "out must not be NULL");
-  // The gather writes straight into out when the device can address it (memory of this
-  // device, or pinned host memory mapped into the device's address space, which on a
-  // coherent host link costs no extra pass); other host memory gets a staged copy.
+  // The gather writes straight into out when it is memory of this device.  Pinned host
+  // memory gets the gather in chunks into the staging buffer, each chunk copied out by
+  // the copy engine (on the capture stream, idle outside lb_ks_step) while the next one is
+  // gathered: the copy engine moves more over the host link than the gather's own stores
+  // to mapped host memory.  Other host memory gets one staged copy.
   double* dst = h->d_stage;
+  bool pinned = false;
   {
     int dev = 0;
     cudaPointerAttributes pa{};
     if (cudaGetDevice(&dev) == cudaSuccess && cudaPointerGetAttributes(&pa, out) == cudaSuccess) {
-      if ((pa.type == cudaMemoryTypeDevice && pa.device == dev) || (pa.type == cudaMemoryTypeHost && pa.devicePointer))
-        dst = static_cast<double*>(pa.devicePointer);
+      if (pa.type == cudaMemoryTypeDevice && pa.device == dev) dst = static_cast<double*>(pa.devicePointer);
+      else if (pa.type == cudaMemoryTypeHost) pinned = true;
     } else {
       cudaGetLastError();
     }
+  }
+  if (pinned && h->rho_chunks.size() > 1) {
+    if (!h->ev_rho) LBKS_CUDA(h, cudaEventCreateWithFlags(&h->ev_rho, cudaEventDisableTiming), "create event");
+    for (size_t c = 0; c + 1 < h->rho_chunks.size(); ++c) {
+      const int t0 = h->rho_chunks[c].first, t1 = h->rho_chunks[c + 1].first;
+      const int64_t o0 = h->rho_chunks[c].second, o1 = h->rho_chunks[c + 1].second;
+      LBKS_CUDA(h, launch_gather_rho(h->nplanes, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles + t0, t1 - t0,
+                                     h->d_stage, h->d_rho_off, h->stream), "gather rho");
+      h->launches += 1;
+      LBKS_CUDA(h, cudaEventRecord(h->ev_rho, h->stream), "record");
+      LBKS_CUDA(h, cudaStreamWaitEvent(h->cap_stream, h->ev_rho, 0), "wait");
+      LBKS_CUDA(h, cudaMemcpyAsync(out + o0, h->d_stage + o0, sizeof(double) * (size_t)(o1 - o0),
+                                   cudaMemcpyDeviceToHost, h->cap_stream), "copy rho");
+    }
+    LBKS_CUDA(h, cudaStreamSynchronize(h->cap_stream), "sync");
+    LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+    return check_flags(h);
   }
   LBKS_CUDA(h, launch_gather_rho(h->nplanes, h->prec, arena(h, h->cur), h->d_runs, h->d_stream_tiles, h->n_stream_tiles,
                                  dst, h->d_rho_off, h->stream), "gather rho");
@@ -1319,6 +1353,7 @@ void lb_ks_free(lb_ks_t* h) {
     if (h->ev_join[l]) cudaEventDestroy(h->ev_join[l]);
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_rho) cudaEventDestroy(h->ev_rho);
   cudaGetLastError();
   delete h;
 }

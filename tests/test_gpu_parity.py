@@ -441,3 +441,29 @@ def test_nonfinite_rho0_is_einval_naming_the_first_run(lb, prec):
                             lb.lb_ks_default_opts(precision=prec, kernel=lb.KERNEL_RESIDENT))
     assert e.value.code == -1
     assert "run 2: rho0 is not finite" in lb.lb_ks_last_error(None)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_rho_into_pinned_device_and_pageable_memory_agree(lb, precision):
+    """lb_ks_rho gathers into device memory directly, into pinned host memory in chunks of
+    tiles copied out while the next chunk is gathered, and into other host memory through
+    one staged copy: the three give the same values bitwise, on a batch whose chunk
+    boundaries fall inside runs."""
+    Ns = np.array([5000, 37, 1 << 15, 12345, 777, 40000, 7, 3001], dtype=np.int64)
+    rng = np.random.default_rng(46)
+    r0 = np.concatenate([0.01 * rng.standard_normal(n) for n in Ns])
+    h = lb.lb_ks_batch_init(7, Ns, Ns * 0.1, np.full(Ns.size, 1e-4), np.linspace(1.5, 2.5, Ns.size),
+                            r0, lb.lb_ks_default_opts(precision=precision, kernel=2))
+    try:
+        lb.lb_ks_step(h, 30)
+        pageable = np.empty(int(Ns.sum()))
+        lb.lb_ks_rho(h, pageable)
+        pinned = torch.full((int(Ns.sum()),), np.nan, dtype=torch.float64).pin_memory()
+        lb.lb_ks_rho(h, pinned)
+        dev = torch.full((int(Ns.sum()),), np.nan, dtype=torch.float64, device="cuda")
+        lb.lb_ks_rho(h, dev)
+    finally:
+        lb.lb_ks_free(h)
+    assert np.all(np.isfinite(pageable))
+    np.testing.assert_array_equal(pinned.numpy(), pageable)
+    np.testing.assert_array_equal(dev.cpu().numpy(), pageable)
