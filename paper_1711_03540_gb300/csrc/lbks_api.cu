@@ -10,9 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
-#include <atomic>
 
 #include "../../include/lb_ks.h"
 #include "lbks_internal.h"
@@ -105,6 +103,9 @@ struct lb_ks {
   std::vector<int64_t> N, rho_off;
   RunTable runs_h;
   std::vector<double> mass0_h;
+  // runs_h's device-computed fields (rhobar, FP16 scale) and mass0_h hold the device's
+  // values: read back when a checkpoint first needs them
+  bool tables_on_host = false;
   int64_t total_sites = 0, plane = 0;
   void* fbuf[2] = {nullptr, nullptr};
   int cur = 0;
@@ -824,31 +825,20 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
   h->rho_off[0] = 0;
   for (int32_t r = 0; r < nruns; ++r) h->rho_off[r + 1] = h->rho_off[r] + N[r];
   h->mass0_h.assign(nruns, 0.0);
-  // arena offsets first (a prefix sum), then the descriptors, on a few host threads for
-  // large batches (each thread writes its own runs, once)
-  const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
-  std::vector<int64_t> run_off(nruns);
+  // Each descriptor is written once, in place (the table's allocator does not zero it).
+  // One thread: spreading the runs over a few host threads saved ~0.1 ms on 4096 runs,
+  // but a new thread sometimes started milliseconds late.
+  h->runs_h.resize(nruns);
   int64_t off = 0;
   for (int32_t r = 0; r < nruns; ++r) {
-    run_off[r] = off + ghost;
-    off += align_up(N[r] + 2 * ghost, kAlign);
-  }
-  h->runs_h.resize(nruns);
-  std::atomic<int32_t> bad_coef{nruns};  // first run whose coefficients are not finite
-  auto fill_runs = [&](int32_t r0, int32_t r1) {
-    for (int32_t r = r0; r < r1; ++r) {
-      RunDesc& d = h->runs_h[r];
-      std::memset(&d, 0, sizeof(d));
-      double A[7], B[7];
-      // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
-      const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
-      if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK) {
-        int32_t cur = bad_coef.load();
-        while (r < cur && !bad_coef.compare_exchange_weak(cur, r)) {
-        }
-        continue;
-      }
-      const double w = 1.0 / tau[r];
+    RunDesc& d = h->runs_h[r];
+    std::memset(&d, 0, sizeof(d));
+    double A[7], B[7];
+    // periodic: N sites on [0, L); reservoir ends: N nodes on [0, L] including both ends
+    const double dx = L[r] / (double)(reservoir ? N[r] - 1 : N[r]);
+    if (lb_ks_params(scheme, dx, dt[r], tau[r], o.dm_variant, A, B, nullptr) != LB_KS_OK)
+      return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(r) + ": coefficients are not finite"));
+    const double w = 1.0 / tau[r];
     d.N = N[r];
     d.reservoir = reservoir ? 1 : 0;
     d.rho_left = reservoir ? rho_left[r] : 0.0;
@@ -861,31 +851,15 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
       d.af[i] = (float)d.a[i];
       d.bf[i] = (float)d.b[i];
     }
-      d.r = 1.0 - w;
-      d.rf = (float)d.r;
-      d.rhobar = 0.0;  // rhobar and the FP16 scale: set on the device
-      d.scale = d.inv_scale = 1.0;
-      d.scalef = d.inv_scalef = 1.0f;
-      d.off = run_off[r];
-    }
-  };
-  {
-    const int nth = nruns >= 1024 ? 4 : 1;
-    std::vector<std::thread> pool;
-    int32_t r0 = 0;
-    try {
-      for (int k = 1; k < nth; ++k) {
-        const int32_t r1 = (int32_t)((int64_t)nruns * k / nth);
-        pool.emplace_back(fill_runs, r0, r1);
-        r0 = r1;
-      }
-    } catch (...) {  // no thread: this one does the rest
-    }
-    fill_runs(r0, nruns);
-    for (std::thread& th : pool) th.join();
+    d.r = 1.0 - w;
+    d.rf = (float)d.r;
+    d.rhobar = 0.0;  // rhobar and the FP16 scale: set on the device
+    d.scale = d.inv_scale = 1.0;
+    d.scalef = d.inv_scalef = 1.0f;
+    const int64_t ghost = reservoir ? cmax : 0;  // ghost nodes stored before node 0 and after node N-1
+    d.off = off + ghost;
+    off += align_up(N[r] + 2 * ghost, kAlign);
   }
-  if (bad_coef.load() < nruns)
-    return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(bad_coef.load()) + ": coefficients are not finite"));
   h->plane = std::max<int64_t>(off, kAlign);
 
   // Tiles.  The streaming tiles (also those of the guard, the statistics of rho0 and the
@@ -1034,9 +1008,7 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
   // rho0's statistics, computed on the device while the host planned
   int bad_run = nruns;
   if ((ce = cudaEventSynchronize(stats.ev)) != cudaSuccess ||
-      (ce = cudaMemcpy(&bad_run, h->d_bad_run, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
-      (ce = cudaMemcpy(h->runs_h.data(), h->d_runs, sizeof(RunDesc) * nruns, cudaMemcpyDeviceToHost)) != cudaSuccess ||
-      (ce = cudaMemcpy(h->mass0_h.data(), h->d_mass0, sizeof(double) * nruns, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      (ce = cudaMemcpy(&bad_run, h->d_bad_run, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return bail(cuda_fail(h, ce, "read rho0 statistics"));
   if (bad_run < nruns) return bail(fail(h, LB_KS_EINVAL, "run " + std::to_string(bad_run) + ": rho0 is not finite"));
   warn_if_linearly_unstable(h, L, dt, tau);
@@ -1225,6 +1197,14 @@ int lb_ks_save(lb_ks_t* h, void* buf, size_t bytes) try {
   p += 64;
   std::memcpy(p, h->N.data(), sizeof(int64_t) * h->nruns);
   p += sizeof(int64_t) * h->nruns;
+  if (!h->tables_on_host) {  // the run constants and initial masses rho0's statistics set
+    LBKS_CUDA(h, cudaMemcpyAsync(h->runs_h.data(), h->d_runs, sizeof(RunDesc) * h->nruns, cudaMemcpyDeviceToHost,
+                                 h->stream), "read run table");
+    LBKS_CUDA(h, cudaMemcpyAsync(h->mass0_h.data(), h->d_mass0, sizeof(double) * h->nruns, cudaMemcpyDeviceToHost,
+                                 h->stream), "read initial masses");
+    LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
+    h->tables_on_host = true;
+  }
   std::memcpy(p, h->runs_h.data(), sizeof(RunDesc) * h->nruns);
   p += sizeof(RunDesc) * h->nruns;
   std::memcpy(p, h->mass0_h.data(), sizeof(double) * h->nruns);
@@ -1274,6 +1254,7 @@ int lb_ks_load(lb_ks_t* h, const void* buf, size_t bytes) try {
   LBKS_CUDA(h, cudaStreamSynchronize(h->stream), "sync");
   h->runs_h.assign(runs.begin(), runs.end());
   h->mass0_h = m0;
+  h->tables_on_host = true;
   LBKS_CUDA(h, cudaMemcpy(h->d_runs, runs.data(), sizeof(RunDesc) * h->nruns, cudaMemcpyHostToDevice), "load runs");
   LBKS_CUDA(h, cudaMemcpy(h->d_mass0, m0.data(), sizeof(double) * h->nruns, cudaMemcpyHostToDevice), "load mass0");
   LBKS_CUDA(h, cudaMemcpy(h->fbuf[h->cur], p, storage_bytes(h->prec) * (size_t)h->nplanes * (size_t)h->plane,
