@@ -129,6 +129,19 @@ def test_reservoir_init_rejects_invalid_arguments(lb, bad):
     assert e.value.code == -1
 
 
+def test_empty_batch_is_einval(lb):
+    """An ensemble of no runs is EINVAL, checked on the host before any device work
+    (periodic and reservoir constructors alike), with a reason and no handle."""
+    e0 = np.zeros(0)
+    with pytest.raises(lb.LbKsError) as e:
+        lb.lb_ks_batch_init(7, np.zeros(0, dtype=np.int64), e0, e0, e0, e0)
+    assert e.value.code == -1
+    assert "nruns" in lb.lb_ks_last_error(None)
+    with pytest.raises(lb.LbKsError) as e:
+        lb.lb_ks_batch_init_reservoir(5, np.zeros(0, dtype=np.int64), e0, e0, e0, e0, e0, e0)
+    assert e.value.code == -1
+
+
 @pytest.mark.parametrize("Ns", [[(1 << 30) + 1], [1 << 30] * 17])
 def test_size_limits_are_einval(lb, Ns):
     """A lattice above 2^30 sites, or more than 2^34 sites in all, is EINVAL before

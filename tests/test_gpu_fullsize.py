@@ -115,7 +115,7 @@ def test_long_lattice_fp32_against_fp64_at_t1(lb, long_lattice):
     """FP32 storage (resident, guard every 500 steps) against the plain FP64 kernel
     (parity-tested against the oracle) after T = 1 (10^4 steps) on all 2^24 sites:
     rel-L2 <= 1e-4, the tolerance for T <= 10 (measured: 1.8e-6 at T = 1, 7.8e-6 at
-    T = 10, tests/measure_long_lattice.py)."""
+    T = 10, by bench.py --workload long --error-to 10)."""
     wl, n = long_lattice, 10_000
     ref, _, _ = _run(lb, wl, n, precision=0, kernel=1)
     got, _, d = _run(lb, wl, n, precision=1, kernel=3, recentre_every=500)
