@@ -74,14 +74,16 @@ cudaError_t launch_init_eq(int Q, int storage, Arena dst, const RunDesc* runs, c
                            int ntiles, const double* rho0, const int64_t* rho_off, cudaStream_t s);
 cudaError_t launch_gather_rho(int Q, int storage, Arena src, const RunDesc* runs, const Tile* tiles,
                               int ntiles, double* out, const int64_t* out_off, cudaStream_t s);
+// threads: the block size, 32..256 (a multiple of 32), at least every tile's length.
 cudaError_t launch_plain_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
-                              const Tile* tiles, int ntiles, cudaStream_t s);
+                              const Tile* tiles, int ntiles, int threads, cudaStream_t s);
 cudaError_t launch_stream_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
                                const Tile* tiles, int ntiles, cudaStream_t s);
 // Lattices with reservoir ends: tiles cover nodes -c_max .. N-1+c_max.  reset_only = 1
 // writes f^eq(rho_bc) into the reservoir nodes of dst and nothing else (initial state).
+// threads: as for launch_plain_step.
 cudaError_t launch_reservoir_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs,
-                                  const Tile* tiles, int ntiles, int reset_only, cudaStream_t s);
+                                  const Tile* tiles, int ntiles, int threads, int reset_only, cudaStream_t s);
 // Initial statistics of rho0 (FP64, staged on the device; tiles cover [0, N) of each run):
 // mass0 per run, rhobar (and for F16S the storage scale) written into runs, and the first
 // run holding a non-finite value atomically min-ed into bad_run (scratch: 2 doubles per tile).

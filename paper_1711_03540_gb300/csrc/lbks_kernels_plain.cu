@@ -609,17 +609,18 @@ cudaError_t launch_gather_rho(int Q, int storage, Arena src, const RunDesc* runs
 }
 
 cudaError_t launch_plain_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
-                              int ntiles, cudaStream_t s) {
+                              int ntiles, int threads, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  if (storage == kF16S) return cudaErrorInvalidValue;
-  LBKS_DISPATCH_Q_ST(Q, storage, (plain_step_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(src, dst, runs, tiles)));
+  if (storage == kF16S || threads < 32 || threads > kPlainThreads || threads % 32) return cudaErrorInvalidValue;
+  LBKS_DISPATCH_Q_ST(Q, storage, (plain_step_kernel<Qc, STc><<<ntiles, threads, 0, s>>>(src, dst, runs, tiles)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_reservoir_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
-                                  int ntiles, int reset_only, cudaStream_t s) {
+                                  int ntiles, int threads, int reset_only, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  LBKS_DISPATCH_Q_ST(Q, storage, (reservoir_step_kernel<Qc, STc><<<ntiles, kPlainThreads, 0, s>>>(
+  if (threads < 32 || threads > kPlainThreads || threads % 32) return cudaErrorInvalidValue;
+  LBKS_DISPATCH_Q_ST(Q, storage, (reservoir_step_kernel<Qc, STc><<<ntiles, threads, 0, s>>>(
                                      src, dst, runs, tiles, reset_only)));
   return cudaGetLastError();
 }
