@@ -28,10 +28,6 @@ namespace {
 
 thread_local std::string g_ctor_error = "no error";
 
-// Sites per tile of the plain family (one thread per site, one block per tile): 256, or
-// for small workloads down to 32 (plain_tile_sites).
-constexpr int kPlainTile = 256;
-constexpr int kPlainTileMin = 32;
 constexpr int kAlign = 32;  // elements: run offsets and the plane stride are multiples of this
 constexpr uint32_t kMagic = 0x534b424cu;  // "LBKS"
 constexpr uint32_t kVersion = 1;
@@ -115,7 +111,7 @@ struct lb_ks {
   RunDesc* d_runs = nullptr;
   Tile* d_plain_tiles = nullptr;
   int n_plain_tiles = 0;
-  int plain_tile = kPlainTile;  // sites per plain-family tile, also its launches' block size
+  int plain_tile = kPlainTileMax;  // sites per plain-family tile, also its launches' block size
   Tile* d_stream_tiles = nullptr;
   int n_stream_tiles = 0;
   int32_t* d_stream_tile_begin = nullptr;
@@ -258,21 +254,6 @@ void dfree(lb_ks* h, T** p) {
 }
 
 Arena arena(lb_ks* h, int which) { return Arena{h->fbuf[which], h->plane}; }
-
-// Sites per plain-family tile: the largest of 256, 128, 64 and 32 that still gives every
-// SM two tiles, else 32.  A small workload (one lattice of a few thousand sites) in
-// 256-site tiles runs on a few SMs, each doing 256 sites' FP64 arithmetic per step at
-// GB300's low FP64 rate, while the rest idle; smaller tiles spread the same per-site
-// work over more SMs.  Results do not depend on the tiling (each thread updates one
-// site on its own).  Reservoir lattices' tiles also cover their 2 c_max ghost nodes.
-int plain_tile_sites(const std::vector<int64_t>& N, bool reservoir, int cmax, int sms) {
-  for (int t = kPlainTile; t > kPlainTileMin; t /= 2) {
-    int64_t tiles = 0;
-    for (int64_t n : N) tiles += (n + (reservoir ? 2 * cmax : 0) + t - 1) / t;
-    if (tiles >= 2 * (int64_t)sms) return t;
-  }
-  return kPlainTileMin;
-}
 
 bool valid_opts(const lb_ks_opts& o, std::string* why) {
   if (o.precision < LB_KS_F64 || o.precision > LB_KS_F16S) { *why = "opts.precision must be 0, 1 or 2"; return false; }
@@ -908,14 +889,8 @@ int create_body(lb_ks*& h, lb_ks_t** out, int scheme, int32_t nruns, const int64
     cudaError_t e1 = cudaGetDevice(&dev);
     if (e1 == cudaSuccess) e1 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e1 != cudaSuccess) return cuda_fail(h, e1, "cudaDeviceGetAttribute");
-    const int tile = plain_tile_sites(h->N, reservoir, cmax, sms);
-    std::vector<Tile> pt;
-    for (int32_t r = 0; r < nruns; ++r) {
-      // reservoir lattices: the plain-family tiles also cover the ghost nodes
-      const int64_t g0 = reservoir ? -cmax : 0, g1 = reservoir ? N[r] + cmax : N[r];
-      for (int64_t x = g0; x < g1; x += tile)
-        pt.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(tile, g1 - x), 0});
-    }
+    int tile = 0;
+    const std::vector<Tile> pt = lbks::plan::plain_tiles(h->N, reservoir, cmax, sms, &tile);
     int rc2;
     if ((rc2 = dalloc(h, &h->d_plain_tiles, pt.size()))) return rc2;
     cudaError_t e2 = cudaMemcpy(h->d_plain_tiles, pt.data(), sizeof(Tile) * pt.size(), cudaMemcpyHostToDevice);

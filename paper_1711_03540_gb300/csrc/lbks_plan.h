@@ -15,6 +15,39 @@
 namespace lbks {
 namespace plan {
 
+// Sites per tile of the plain kernel family (one thread per site, one block per tile).
+constexpr int kPlainTileMax = 256;
+constexpr int kPlainTileMin = 32;
+
+// Sites per plain-family tile: the largest of 256, 128, 64 and 32 that still gives every
+// SM two tiles, else 32.  A small workload (one lattice of a few thousand sites) in
+// 256-site tiles runs on a few SMs, each doing 256 sites' FP64 arithmetic per step at
+// GB300's low FP64 rate, while the rest idle; smaller tiles spread the same per-site
+// work over more SMs.  Results do not depend on the tiling (each thread updates one
+// site on its own).  Reservoir lattices' tiles also cover their 2 c_max ghost nodes.
+inline int plain_tile_sites(const std::vector<int64_t>& Ns, bool reservoir, int cmax, int sms) {
+  for (int t = kPlainTileMax; t > kPlainTileMin; t /= 2) {
+    int64_t tiles = 0;
+    for (int64_t n : Ns) tiles += (n + (reservoir ? 2 * cmax : 0) + t - 1) / t;
+    if (tiles >= 2 * (int64_t)sms) return t;
+  }
+  return kPlainTileMin;
+}
+
+// The plain family's tiles: run by run, consecutive stretches of plain_tile_sites sites
+// (the last one of a run shorter) covering [0, N) of each run, or [-c_max, N + c_max)
+// for reservoir lattices; *tile receives the tile length (the launches' block size).
+inline std::vector<Tile> plain_tiles(const std::vector<int64_t>& Ns, bool reservoir, int cmax, int sms, int* tile) {
+  const int t = plain_tile_sites(Ns, reservoir, cmax, sms);
+  std::vector<Tile> pt;
+  for (int32_t r = 0; r < (int32_t)Ns.size(); ++r) {
+    const int64_t g0 = reservoir ? -cmax : 0, g1 = reservoir ? Ns[r] + cmax : Ns[r];
+    for (int64_t x = g0; x < g1; x += t) pt.push_back(Tile{r, (int32_t)x, (int32_t)std::min<int64_t>(t, g1 - x), 0});
+  }
+  *tile = t;
+  return pt;
+}
+
 // One half of a ring of N sites for a cluster pair: own sites [x_own, x_own + len) of
 // the ring with `halo` sites on each side, lengthened on the right until it splits
 // into runs of S and S-1 sites; false if that takes more than NT threads.

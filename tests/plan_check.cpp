@@ -6,7 +6,12 @@
 // 1 to put single-block bundles two to a pair) and prints one line per case:
 //     OK rings=<pieces> halves=<lattices> spans=<rings across a pair> segs=<pieces> blocks=<groups>
 //        pairs=<groups> segblocks=<groups> ring_threads=<threads> seg_threads=<threads>
-// or FAIL <reason>.  The line "FIRSTFIT <trials> <seed>" compares the groups' first
+// or FAIL <reason>.  The line "PLAIN <SMs> <reservoir 0|1> <c_max> N_0 ... N_{n-1}" checks
+// the plain family's tiles (every site, ghosts of reservoir lattices included, in
+// exactly one tile of its run; lengths within the chosen tile size; the size the
+// largest of 256, 128, 64, 32 giving two tiles per SM, else 32) and prints
+//     OK tile=<sites> tiles=<count>
+// The line "FIRSTFIT <trials> <seed>" compares the groups' first
 // fit with a linear scan of the groups on random pieces; "ORDER <trials> <seed>" the
 // counting sort that orders pieces and bundles with a stable sort.
 #include <algorithm>
@@ -223,6 +228,38 @@ std::string order_trials(int trials, unsigned seed) {
 
 }  // namespace
 
+// The plain family's tiles for one set of runs.
+std::string plain_case(int sms, bool reservoir, int C, const std::vector<int64_t>& Ns) {
+  fail_.clear();
+  int tile = 0;
+  const std::vector<lbks::Tile> pt = plain_tiles(Ns, reservoir, C, sms, &tile);
+  check(tile == 32 || tile == 64 || tile == 128 || tile == 256, "tile size not a power of two in [32, 256]");
+  auto count = [&](int t) {
+    int64_t n = 0;
+    for (int64_t N : Ns) n += (N + (reservoir ? 2 * C : 0) + t - 1) / t;
+    return n;
+  };
+  check(tile == 32 || count(tile) >= 2 * (int64_t)sms, "fewer than two tiles per SM above the smallest size");
+  check(tile == 256 || count(2 * tile) < 2 * (int64_t)sms, "a larger tile would still give two tiles per SM");
+  std::vector<std::vector<int>> hits(Ns.size());
+  for (size_t r = 0; r < Ns.size(); ++r) hits[r].assign((size_t)(Ns[r] + (reservoir ? 2 * C : 0)), 0);
+  const int64_t g0 = reservoir ? -C : 0;
+  for (const lbks::Tile& t : pt) {
+    if (!check(t.run >= 0 && t.run < (int)Ns.size(), "tile of an unknown run")) break;
+    check(t.len >= 1 && t.len <= tile, "tile length outside [1, tile size]");
+    for (int k = 0; k < t.len; ++k) {
+      const int64_t x = (int64_t)t.x0 + k - g0;
+      if (!check(x >= 0 && x < (int64_t)hits[t.run].size(), "tile outside its run")) break;
+      ++hits[t.run][(size_t)x];
+    }
+  }
+  for (size_t r = 0; r < Ns.size() && fail_.empty(); ++r)
+    for (int h : hits[r])
+      if (!check(h == 1, "run " + std::to_string(r) + ": a site in " + std::to_string(h) + " tiles")) break;
+  if (!fail_.empty()) return "FAIL " + fail_;
+  return "OK tile=" + std::to_string(tile) + " tiles=" + std::to_string(pt.size());
+}
+
 int main() {
   std::string line;
   while (std::getline(std::cin, line)) {
@@ -235,6 +272,15 @@ int main() {
       unsigned seed = 0;
       in >> trials >> seed;
       std::cout << first_fit_trials(trials, seed) << "\n";
+      continue;
+    }
+    if (head == "PLAIN") {
+      int sms = 0, res = 0, C = 0;
+      in >> sms >> res >> C;
+      std::vector<int64_t> Ns;
+      int64_t v;
+      while (in >> v) Ns.push_back(v);
+      std::cout << plain_case(sms, res != 0, C, Ns) << "\n";
       continue;
     }
     if (head == "ORDER") {

@@ -4,8 +4,9 @@ ensemble's lengths and on edge sets, that every site is stored by exactly one
 piece, that pieces split into runs of S and S-1 sites per thread, that halves and
 segments carry halos wide enough for the steps between exchanges, that groups hold
 disjoint thread ranges within their capacity, that the segment-tree first fit
-chooses the same group as a linear scan, and that the counting sort ordering pieces
-and bundles gives a stable sort's order.  No GPU needed."""
+chooses the same group as a linear scan, that the counting sort ordering pieces
+and bundles gives a stable sort's order, and that the plain kernel family's tiles
+cover every site once at the tile size its rule picks.  No GPU needed."""
 import os
 import shutil
 import subprocess
@@ -103,3 +104,24 @@ def test_first_fit_matches_linear_scan(checker):
 
 def test_counting_order_matches_stable_sort(checker):
     checker(["ORDER 200 21", "ORDER 200 22"])
+
+
+def test_plain_family_tiles(checker):
+    """The plain family's tiles cover every site once (reservoir lattices with their
+    c_max ghosts on each side) and take the largest size of 256, 128, 64, 32 sites that
+    gives each of 152 SMs two tiles: one 4096-site lattice (config 2) and one 512-site
+    lattice (config 1) in 32-site tiles, the 4096-lattice ensemble in 256."""
+    from paper_1711_03540_gb300 import workloads
+
+    ens = workloads.ensemble(4096).N
+    lines = ["PLAIN 152 0 3 4096", "PLAIN 152 0 2 512", "PLAIN 152 0 3 " + " ".join(map(str, ens)),
+             "PLAIN 152 1 3 1201 601 301", "PLAIN 152 0 3 7", "PLAIN 152 1 2 5",
+             "PLAIN 152 0 3 20000", "PLAIN 152 0 3 40000", "PLAIN 152 0 3 " + " ".join(["5000"] * 8),
+             "PLAIN 152 0 3 " + " ".join(["300"] * 160), "PLAIN 152 0 3 " + " ".join(["64"] * 100)]
+    res = checker(lines)
+    assert res[0] == {"tile": "32", "tiles": "128"}
+    assert res[1] == {"tile": "32", "tiles": "16"}
+    assert res[2]["tile"] == "256"
+    assert res[3] == {"tile": "32", "tiles": "67"}  # (1201 + 6) / 32 rounded up, and so on
+    assert [r["tile"] for r in res[6:]] == ["64", "128", "128", "256", "32"]
+
