@@ -98,4 +98,35 @@ __device__ __forceinline__ int64_t wrap_site(int64_t x, int64_t N) {
   return x < 0 ? x + N : (x >= N ? x - N : x);
 }
 
+// Programmatic dependent launch (PTX ISA: griddepcontrol), for the kernels that run one
+// step per launch (plain, reservoir, streaming, tau = 1 streaming).  They are launched
+// with programmatic stream serialisation (launch_early), so that the next step's grid is
+// scheduled while this one runs instead of after it.  Every thread first waits until
+// the grid before it in the stream (the previous step, which reads this step's
+// destination and writes its source) has completed and its writes are visible; only
+// then does it touch global memory and let the next grid be scheduled.  In a grid
+// launched without the attribute both instructions return at once.
+__device__ __forceinline__ void wait_prior_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with programmatic stream serialisation allowed (for kernels that start with
+// wait_prior_grid): the grid may be scheduled before the kernel ahead of it in the
+// stream has finished.  Other work in the stream (copies, event waits) orders it fully.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_early(void (*kernel)(KArgs...), int grid, int threads, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace lbks

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kCollapseThreads) collapse_step_kernel(Arena s
   using T = typename StorageType<ST>::type;
   using CT = typename StorageType<ST>::compute;
   __shared__ CT buf[kCollapseTile + 2 * C];
+  wait_prior_grid();
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
   const T* fs = static_cast<const T*>(src.f) + d.off;
@@ -98,12 +99,11 @@ cudaError_t launch_collapse_init(int storage, Arena dst, const RunDesc* runs, co
 cudaError_t launch_collapse_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
                                  int ntiles, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  if (Q == 5 && storage == kF64) collapse_step_kernel<2, kF64><<<ntiles, kCollapseThreads, 0, s>>>(src, dst, runs, tiles);
-  else if (Q == 5 && storage == kF32) collapse_step_kernel<2, kF32><<<ntiles, kCollapseThreads, 0, s>>>(src, dst, runs, tiles);
-  else if (Q == 7 && storage == kF64) collapse_step_kernel<3, kF64><<<ntiles, kCollapseThreads, 0, s>>>(src, dst, runs, tiles);
-  else if (Q == 7 && storage == kF32) collapse_step_kernel<3, kF32><<<ntiles, kCollapseThreads, 0, s>>>(src, dst, runs, tiles);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  if (Q == 5 && storage == kF64) return launch_early(collapse_step_kernel<2, kF64>, ntiles, kCollapseThreads, 0, s, src, dst, runs, tiles);
+  if (Q == 5 && storage == kF32) return launch_early(collapse_step_kernel<2, kF32>, ntiles, kCollapseThreads, 0, s, src, dst, runs, tiles);
+  if (Q == 7 && storage == kF64) return launch_early(collapse_step_kernel<3, kF64>, ntiles, kCollapseThreads, 0, s, src, dst, runs, tiles);
+  if (Q == 7 && storage == kF32) return launch_early(collapse_step_kernel<3, kF32>, ntiles, kCollapseThreads, 0, s, src, dst, runs, tiles);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace lbks

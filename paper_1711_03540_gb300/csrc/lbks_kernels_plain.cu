@@ -150,18 +150,6 @@ __global__ void __launch_bounds__(kPlainThreads) gather_rho_kernel(Arena src, co
   }
 }
 
-// Programmatic dependent launch (PTX ISA: griddepcontrol).  The step kernels of this
-// family are launched with programmatic stream serialisation (launch_early), so that
-// the next step's grid is scheduled while this one runs instead of after it.  Every
-// thread first waits until the grid before it in the stream (the previous step, which
-// reads this step's destination and writes its source) has completed and its writes are
-// visible, and only then touches global memory and lets the next grid be scheduled.
-// In a grid launched without the attribute both instructions return at once.
-__device__ __forceinline__ void wait_prior_grid() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // The plain fused step: one thread per site reads its Q populations, collides
 // (Eq. LB_equation_ordinary) and pushes f*_i to site x + c_i (mod N).
 template <int Q, int ST>
@@ -622,36 +610,18 @@ cudaError_t launch_gather_rho(int Q, int storage, Arena src, const RunDesc* runs
   return cudaGetLastError();
 }
 
-// Launch with programmatic stream serialisation allowed (the kernel starts with
-// wait_prior_grid): the grid may be scheduled before the kernel before it in the stream
-// has finished.  Other work in the stream (copies, event waits) still orders it fully.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_early(void (*kernel)(KArgs...), int grid, int threads, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)threads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 cudaError_t launch_plain_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
                               int ntiles, int threads, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   if (storage == kF16S || threads < 32 || threads > kPlainThreads || threads % 32) return cudaErrorInvalidValue;
-  LBKS_DISPATCH_Q_ST(Q, storage, return launch_early(plain_step_kernel<Qc, STc>, ntiles, threads, s, src, dst, runs, tiles));
+  LBKS_DISPATCH_Q_ST(Q, storage, return launch_early(plain_step_kernel<Qc, STc>, ntiles, threads, 0, s, src, dst, runs, tiles));
 }
 
 cudaError_t launch_reservoir_step(int Q, int storage, Arena src, Arena dst, const RunDesc* runs, const Tile* tiles,
                                   int ntiles, int threads, int reset_only, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   if (threads < 32 || threads > kPlainThreads || threads % 32) return cudaErrorInvalidValue;
-  LBKS_DISPATCH_Q_ST(Q, storage, return launch_early(reservoir_step_kernel<Qc, STc>, ntiles, threads, s, src, dst,
+  LBKS_DISPATCH_Q_ST(Q, storage, return launch_early(reservoir_step_kernel<Qc, STc>, ntiles, threads, 0, s, src, dst,
                                                      runs, tiles, reset_only));
 }
 

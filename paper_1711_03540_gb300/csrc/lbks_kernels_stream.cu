@@ -122,6 +122,7 @@ __device__ __forceinline__ void stream_step(Arena src, Arena dst, const RunDesc*
     else *p = v;
   };
 
+  wait_prior_grid();
   const Tile tl = tiles[blockIdx.x];
   const RunDesc& d = runs[tl.run];
   const Coef<CT, Q> k = load_coef<CT, Q>(d);
@@ -274,10 +275,11 @@ cudaError_t prepare_stream_t() {
 template <int Q, int ST>
 cudaError_t launch_stream_t(Arena src, Arena dst, const RunDesc* runs, const Tile* tiles, int ntiles, cudaStream_t s) {
   if constexpr (ST == kF16S)
-    stream_step_kernel_f16<Q><<<ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s>>>(src, dst, runs, tiles);
+    return launch_early(stream_step_kernel_f16<Q>, ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s, src, dst,
+                        runs, tiles);
   else
-    stream_step_kernel<Q, ST><<<ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s>>>(src, dst, runs, tiles);
-  return cudaGetLastError();
+    return launch_early(stream_step_kernel<Q, ST>, ntiles, StreamShape<ST>::kThreads, stream_smem<Q, ST>(), s, src, dst,
+                        runs, tiles);
 }
 
 }  // namespace
